@@ -1,0 +1,200 @@
+"""Pins for the FP64 oracle against facts fixed by the paper and by algebra,
+none of which re-types the oracle's own unfold-and-multiply code.
+
+* brute force of eq. 3.2 over every multi-index (ivec written out per eq. 2.1);
+* the hand-worked integer example in tests/golden/;
+* closed form of eq. 2.13 with E = 0 for an exact CP tensor;
+* the invariant sum_i a_r^(n)[i] g_r^(n)[i] = Y x {a_r} for all n (eq. 2.6);
+* N = 2: G^(1) = Y A^(2), G^(2) = Y^T A^(1);
+* ALS (eq. 2.14): Eckart-Young on matrices, fit -> 1 on noiseless CP tensors,
+  monotone cost, cheap fit formula = explicit fit.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import cpsynth
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def ivec(idx, I):
+    """eq. 2.1, 0-based: i = i_1 + sum_n i_n * prod_{j<n} I_j."""
+    lin, stride = 0, 1
+    for i, n in zip(idx, I):
+        lin += i * stride
+        stride *= n
+    return lin
+
+
+def brute_gradient(y, I, A, n):
+    """eq. 3.2 evaluated term by term in pure Python."""
+    R = A[0].shape[1]
+    G = np.zeros((I[n], R))
+    for idx in itertools.product(*[range(v) for v in I]):
+        yv = float(y[ivec(idx, I)])
+        for r in range(R):
+            p = yv
+            for m, im in enumerate(idx):
+                if m != n:
+                    p *= A[m][im, r]
+            G[idx[n], r] += p
+    return G
+
+
+def multi_tvp(y, I, A, r):
+    """Y x_1 a^(1) x_2 ... x_N a^(N) (eq. 2.6) by contracting one mode at a time."""
+    T = np.asarray(y, dtype=np.float64).reshape(I, order="F")
+    for m in range(len(I)):
+        T = np.tensordot(T, A[m][:, r], axes=([0], [0]))
+    return float(T)
+
+
+SHAPES = [
+    ([3, 2], 1), ([2, 5], 3), ([1, 4], 2), ([3, 1, 2], 2), ([2, 3, 5], 3),
+    ([5, 2, 3], 1), ([2, 2, 3, 2], 2), ([3, 1, 2, 5], 3), ([2, 3, 2, 2, 3], 2),
+    ([1, 2, 1, 3, 2], 1),
+]
+
+
+@pytest.mark.parametrize("I,R", SHAPES)
+def test_gradient_matches_bruteforce(I, R):
+    g = cpsynth.rng(7, len(I), R)
+    y = g.standard_normal(int(np.prod(I)))
+    A = [g.standard_normal((v, R)) for v in I]
+    for n in range(len(I)):
+        Gb = brute_gradient(y, I, A, n)
+        Go = oracle.cp_gradient(y, I, A, n)
+        np.testing.assert_allclose(Go, Gb, rtol=1e-12, atol=1e-12)
+        for i in range(I[n]):
+            for r in range(R):
+                assert oracle.cp_gradient_entry(y, I, A, n, i, r) == pytest.approx(Gb[i, r], rel=1e-12, abs=1e-12)
+
+
+def test_golden_worked_example():
+    with open(os.path.join(GOLDEN, "worked_example_3d.json")) as f:
+        ex = json.load(f)
+    I = ex["I"]
+    y = np.array(ex["vecY"], dtype=np.float64)
+    A = [np.array(a, dtype=np.float64) for a in ex["A"]]
+    for n in range(len(I)):
+        G = oracle.cp_gradient(y, I, A, n)
+        np.testing.assert_array_equal(G, np.array(ex["G"][n], dtype=np.float64))
+        np.testing.assert_array_equal(np.sum(A[n] * G, axis=0), np.array(ex["inner"], dtype=np.float64))
+
+
+@pytest.mark.parametrize("I,R", [([4, 5, 6], 3), ([3, 4, 2, 5], 4), ([2, 3, 4, 3, 2], 2), ([6, 7], 5)])
+def test_closed_form_exact_cp(I, R):
+    """eq. 2.13 with E = 0: Y_(n) KR = A^(n) (Hadamard_{m != n} A^(m)T A^(m))."""
+    A = cpsynth.gaussian_factors(I, R, seed=11)
+    y = cpsynth.cp_model_vec(A)
+    for n in range(len(I)):
+        V = np.ones((R, R))
+        for m in range(len(I)):
+            if m != n:
+                V *= A[m].T @ A[m]
+        want = A[n] @ V
+        got = oracle.cp_gradient(y, I, A, n)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("I,R", [([5, 4, 3], 3), ([3, 3, 3, 3], 2), ([2, 5, 3, 2, 2], 4)])
+def test_invariant_inner_product(I, R):
+    g = cpsynth.rng(3, len(I))
+    y = g.standard_normal(int(np.prod(I)))
+    A = [g.standard_normal((v, R)) for v in I]
+    want = np.array([multi_tvp(y, I, A, r) for r in range(R)])
+    for n in range(len(I)):
+        G = oracle.cp_gradient(y, I, A, n)
+        np.testing.assert_allclose(np.sum(A[n] * G, axis=0), want, rtol=1e-11, atol=1e-11)
+
+
+def test_matrix_case():
+    g = cpsynth.rng(5)
+    I, R = [7, 9], 4
+    y = g.standard_normal(63)
+    A = [g.standard_normal((v, R)) for v in I]
+    Y = y.reshape(I, order="F")
+    np.testing.assert_allclose(oracle.cp_gradient(y, I, A, 0), Y @ A[1], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle.cp_gradient(y, I, A, 1), Y.T @ A[0], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("I,k", [([100] * 4, 2), ([60] * 5, 2), ([15] * 7, 3), ([30, 40, 50], 1),
+                                 ([100, 2], 1), ([2, 100], 1), ([2, 2], 1), ([1, 1, 1], 2),
+                                 ([3, 4, 5, 6, 7], 2), ([10, 10, 10, 10, 10, 10, 10], 3)])
+def test_split_point(I, k):
+    assert oracle.split_point(I) == k
+
+
+def test_mode_order():
+    assert oracle.als_mode_order([100] * 4) == [1, 0, 2, 3]
+    assert oracle.als_mode_order([15] * 7) == [2, 1, 0, 3, 4, 5, 6]
+    assert oracle.als_mode_order([30, 40, 50]) == [0, 1, 2]
+
+
+def test_als_eckart_young():
+    """N = 2: ALS on a matrix converges to its best rank-R approximation, whose
+    residual is given by the trailing singular values."""
+    g = cpsynth.rng(21)
+    U, _ = np.linalg.qr(g.standard_normal((12, 12)))
+    V, _ = np.linalg.qr(g.standard_normal((9, 9)))
+    s = np.array([9.0, 7.0, 5.0, 3.0, 1.0, 0.5, 0.3, 0.2, 0.1])
+    Y = U[:, :9] @ np.diag(s) @ V.T
+    y = np.reshape(Y, -1, order="F")
+    R = 3
+    A0 = [g.standard_normal((12, R)), g.standard_normal((9, R))]
+    tr = oracle.cp_als(y, [12, 9], A0, iters=200, direct_fit=True)
+    want = 1.0 - np.sqrt(np.sum(s[R:] ** 2)) / np.sqrt(np.sum(s ** 2))
+    assert tr.fits[-1] == pytest.approx(want, abs=1e-9)
+    assert tr.fits_direct[-1] == pytest.approx(want, abs=1e-9)
+
+
+def test_als_noiseless_fit_to_one_and_monotone():
+    I, R = [8, 9, 7, 6], 3
+    A = cpsynth.gaussian_factors(I, R, seed=4)
+    y = cpsynth.cp_model_vec(A)
+    # Starts 6 and 7 converge; start 5 sits in a swamp (a slow-progress stretch
+    # that ALS is known for, end of Section 5) and is only checked for monotonicity.
+    for seed, converges in ((6, True), (7, True), (5, False)):
+        A0 = cpsynth.gaussian_factors(I, R, seed=seed)
+        tr = oracle.cp_als(y, I, A0, iters=150, direct_fit=True)
+        if converges:
+            assert tr.fits[-1] > 1 - 1e-8
+        d = np.array(tr.fits_direct)
+        assert np.all(np.diff(d) >= -1e-12)
+        np.testing.assert_allclose(tr.fits, tr.fits_direct, atol=1e-9)
+        for n in range(len(I)):
+            np.testing.assert_allclose(np.linalg.norm(tr.A[n], axis=0), 1.0, rtol=1e-12)
+
+
+def test_als_cheap_fit_equals_direct_noisy():
+    p = cpsynth.make_problem([6, 7, 8], 4, snr_db=10.0, seed=9, dtype=np.float64)
+    tr = oracle.cp_als(p.y, p.I, p.init, iters=8, direct_fit=True)
+    np.testing.assert_allclose(tr.fits, tr.fits_direct, rtol=1e-10, atol=1e-12)
+    assert np.all(np.diff(tr.fits_direct) >= -1e-12)
+
+
+def test_als_rank_one_is_power_iteration_on_matrix():
+    """R = 1 on a matrix: ALS is the power method, so the model is the top
+    singular triplet sigma_1 u v^T."""
+    g = cpsynth.rng(33)
+    Y = g.standard_normal((10, 8))
+    y = np.reshape(Y, -1, order="F")
+    tr = oracle.cp_als(y, [10, 8], [g.standard_normal((10, 1)), g.standard_normal((8, 1))], iters=300)
+    s = np.linalg.svd(Y, compute_uv=False)
+    assert tr.lam[0] == pytest.approx(s[0], rel=1e-9)
+
+
+def test_cp_full_layout():
+    """cp_full and the synthetic generator agree on the layout of eq. 2.1."""
+    I, R = [3, 4, 2], 2
+    A = cpsynth.gaussian_factors(I, R, seed=2)
+    y = oracle.cp_full(A)
+    for idx in itertools.product(*[range(v) for v in I]):
+        want = sum(np.prod([A[m][idx[m], r] for m in range(3)]) for r in range(R))
+        assert y[ivec(idx, I)] == pytest.approx(want, rel=1e-12, abs=1e-14)
+    np.testing.assert_allclose(cpsynth.cp_model_vec(A), y, rtol=1e-12, atol=1e-14)
