@@ -1,0 +1,400 @@
+"""Benchmark: all-mode CP gradient + fast CP_ALS on the 4-D 100^4, R = 10 FP32 workload.
+
+One step = one all-mode gradient (Algorithm 2) at the starting factors plus
+50 fast CP_ALS sweeps (Section 4) from that start, on a seeded rank-10 CP
+model with N(0,1) factors plus 20 dB Gaussian noise (400 MB tensor, larger
+than L2, so no flush is needed between steps).
+
+value = algorithmic GFLOP/s of the step (2 flops per multiply-add of the
+method's contractions; the R x R solves are not counted), timed with CUDA
+events on the launch stream between barriers.  e2e = the same metric with
+the tensor copied host->device and the results copied back inside every step.
+The roofline object reports the leading contraction (the kernel that streams
+Y, about 99% of the step's bytes): algorithmic bytes per launch = 4 * prod(I)
+over the event-timed duration of each of its launches in the timed region.
+
+--impl reference times the FP64 CPU oracle (explicit unfoldings and
+Khatri-Rao products, Algorithm 1 + eq. 2.14) on the same workload, a bounded
+sample per step (one all-mode gradient and one ALS sweep).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cpsynth  # noqa: E402
+
+WORKLOAD = "cp4d_100_r10_fp32"
+ALS_ITERS = 50
+METRIC = "all-mode CP-gradient GFLOP/s, % roofline; CP-ALS iter/s at stated rel. error"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def prod(v):
+    p = 1
+    for x in v:
+        p *= int(x)
+    return p
+
+
+def split_point(I):
+    best = 0
+    for n in range(1, len(I) + 1):
+        if prod(I[:n]) <= prod(I[n:]):
+            best = n
+    return min(max(best, 1), len(I) - 1)
+
+
+def gradient_flops(I, R):
+    """2 flops per multiply-add of Algorithm 2: both leading contractions over
+    all of Y, then each recursion and finishing contraction over R^(n)/L^(n)."""
+    N, k, P = len(I), split_point(I), prod(I)
+    f = 2 * 2 * R * P
+    for n in range(k, 0, -1):          # right side: R^(n) has prod(I[:n]) entries per rank
+        f += 2 * R * prod(I[:n]) * (2 if n > 1 else 1)
+    for n in range(k, N):              # left side: L^(n) has prod(I[n:]) entries per rank
+        f += 2 * R * prod(I[n:]) * (2 if n < N - 1 else 1)
+    return f
+
+
+def als_sweep_flops(I, R):
+    """One fast ALS sweep: the two leading passes plus the chain contractions."""
+    return gradient_flops(I, R)
+
+
+def step_flops(I, R, iters):
+    return gradient_flops(I, R) + iters * als_sweep_flops(I, R)
+
+
+# ---- clocks ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- CPU oracle baseline ------------------------------------------------------------------
+def openblas_threads():
+    """Threads numpy's BLAS will use (its OpenBLAS build), else the CPU count."""
+    try:
+        import numpy.linalg  # noqa: F401
+        libs = [ln.split()[-1] for ln in open("/proc/self/maps") if "openblas" in ln.lower()]
+        for path in dict.fromkeys(libs):
+            L = ctypes.CDLL(path)
+            for sym in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_",
+                        "openblas_get_num_threads", "scipy_openblas_get_num_threads"):
+                if hasattr(L, sym):
+                    fn = getattr(L, sym)
+                    fn.restype = ctypes.c_int
+                    return int(fn())
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_sample(p):
+    """One all-mode gradient (Algorithm 1 per mode) + one ALS sweep of the oracle; seconds."""
+    import oracle
+    y = p.y.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.cp_gradient_all(y, p.I, p.init)
+    oracle.cp_als(y, p.I, p.init, iters=1)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p):
+    dt = oracle_sample(p)
+    flops = gradient_flops(p.I, p.R) + als_sweep_flops(p.I, p.R)
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": openblas_threads(), "kind": "oracle",
+            "sample": f"one all-mode gradient + one ALS sweep of the FP64 oracle on the full {p.I} R={p.R} "
+                      f"tensor ({dt:.1f} s); flops counted as for the GPU step"}
+
+
+# ---- reference arm -----------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = cpsynth.workload(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_sample(p)
+    times = [oracle_sample(p) for _ in range(args.steps)]
+    flops = gradient_flops(p.I, p.R) + als_sweep_flops(p.I, p.R)
+    ms = 1e3 * sum(times) / len(times)
+    v = flops / (ms / 1e3) / 1e9
+    cores = openblas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4-D FP32 tensor 100x100x100x100 (rank-10 CP model + 20 dB noise), R=10, "
+                                   "oracle step = one all-mode gradient + one ALS sweep", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: one all-mode gradient (Algorithm 1 per mode) + one ALS sweep, "
+                                       "full tensor"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- GPU arm ---------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1204_1586_gb300 as cg
+    cg.lib()
+
+    # Each rank decomposes its own tensor (independent problems: weak scaling, no data-path collective).
+    p = cpsynth.workload(WORKLOAD, seed=cpsynth.DEFAULT_SEED + rank)
+    I, R = p.I, p.R
+    Y = torch.from_numpy(p.y).to(dev)
+    A0 = [cg.colmajor(torch.from_numpy(a.astype(np.float32)).to(dev)) for a in p.init]
+    A = [a.clone() for a in A0]
+    G = [torch.empty((R, In), dtype=torch.float32, device=dev).t() for In in I]
+    lam = torch.ones(R, dtype=torch.float64, device=dev)
+    fit = torch.zeros(ALS_ITERS, dtype=torch.float64, device=dev)
+    ws = cg.Workspace(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(Yd):
+        cg.cp_gradient_all(Yd, I, A0, G, workspace=ws)
+        for a, a0 in zip(A, A0):
+            a.copy_(a0)
+        cg.cp_als_iter(Yd, I, A, ALS_ITERS, lam, fit, workspace=ws)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(Y)
+    barrier()
+
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    cg.launch_count(reset=True)
+    cg.profile_lead(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(Y)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = cg.launch_count()
+    lead = cg.profile_read()
+    cg.profile_lead(False)
+    clocks = clk.stop()
+
+    # end to end: host tensor in pinned memory, copies inside the step
+    Yh = torch.from_numpy(p.y).pin_memory()
+    Ad_h = [a.cpu().pin_memory() for a in A0]
+    out_h = [torch.empty((R, In), dtype=torch.float32).pin_memory() for In in I]
+    fit_h = torch.empty(ALS_ITERS, dtype=torch.float64).pin_memory()
+    Ye = torch.empty_like(Y)
+
+    def step_e2e():
+        Ye.copy_(Yh, non_blocking=True)
+        for a, h in zip(A0, Ad_h):
+            a.copy_(h, non_blocking=True)
+        step(Ye)
+        for g, h in zip(A, out_h):
+            h.copy_(g.t(), non_blocking=True)
+        fit_h.copy_(fit, non_blocking=True)
+
+    step_e2e()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_e2e()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    h2d = Yh.numel() * 4 + sum(a.numel() * 4 for a in Ad_h)
+    d2h = sum(h.numel() * 4 for h in out_h) + fit_h.numel() * 8
+
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    flops = step_flops(I, R, ALS_ITERS)
+    value = world * flops / (ms / 1e3) / 1e9
+    value_e2e = world * flops / (ms_e2e / 1e3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = peaks()
+    ybytes = 4 * prod(I)
+    lead_ms = [t for t, _ in lead]
+    per_side = {}
+    for t, s in lead:
+        per_side.setdefault({1: "step4_R", 2: "step7_L", 3: "step4+7_fused"}[s], []).append(t)
+    avg = sum(lead_ms) / len(lead_ms) if lead_ms else float("nan")
+    achieved = ybytes / (avg / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "lead_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "lead_simt_kernel (Algorithm 2 steps 4/7)",
+                "launches": len(lead_ms),
+                "per_variant_GBps": {k: ybytes / (sum(v) / len(v) / 1e3) / 1e9 for k, v in per_side.items()}}
+
+    check = {}
+    if not args.no_check:
+        import oracle
+        Gc = cg.cp_gradient_all(Y, I, A0, workspace=ws)
+        torch.cuda.synchronize()
+        want = oracle.cp_gradient_all(p.y.astype(np.float64), I, p.init)
+        check["gradient_rel_err_max"] = max(
+            float(np.linalg.norm(Gc[n].double().cpu().numpy() - want[n]) / np.linalg.norm(want[n]))
+            for n in range(len(I)))
+        Ac = [a.clone() for a in A0]
+        _, fc = cg.cp_als_iter(Y, I, Ac, 2, workspace=ws)
+        tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=2)
+        check["als_fit_abs_err_2sweeps"] = float(np.max(np.abs(fc.cpu().numpy() - np.array(tr.fits))))
+        check["als_final_fit"] = float(fit.cpu().numpy()[-1])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "4-D FP32 tensor 100x100x100x100, rank-10 CP model (N(0,1) factors) + 20 dB noise, "
+                               "R=10: one all-mode gradient + 50 fast CP_ALS sweeps per step",
+                   "I": I, "R": R, "split_k": split_point(I), "precision": "fp32", "als_iters": ALS_ITERS,
+                   "l2": "inputs larger than L2 (400 MB tensor)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "gradient_gflops": gradient_flops(I, R) / 1e9,
+        "als_iter_per_s": None,
+        "roofline": roofline,
+        "e2e": {"value": value_e2e, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "check": check,
+    }
+    # per-component timing outside the timed region (informational)
+    tg = _time_component(lambda: cg.cp_gradient_all(Y, I, A0, G, workspace=ws), stream)
+    ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 10, workspace=ws), stream) / 10
+    line["gradient_ms"] = tg
+    line["gradient_gflops"] = gradient_flops(I, R) / (tg / 1e3) / 1e9
+    line["gradient_frac_of_one_pass_roofline"] = (ybytes / hbm / 1e6) / tg
+    line["als_iter_per_s"] = 1e3 / ta
+    line["als_frac_of_two_pass_roofline"] = (2 * ybytes / hbm / 1e6) / ta
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time_component(fn, stream, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * cpgrad -- fast all-mode CP gradients and CP_ALS on NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the CP gradient of a dense N-way tensor Y
+ * (eq. 2.13, product term; Section 2.2):
+ *
+ *     G^(n) = Y_(n) (A^(N) (.) ... (.) A^(n+1) (.) A^(n-1) (.) ... (.) A^(1)),
+ *
+ * for one mode or for every mode, following Algorithm 2 (Section 3.3): the
+ * tensor is viewed, without moving data, as the J x K matrix
+ * reshape(Y, [J_k, K_k]) (eq. 2.3) at a split k, one leading contraction on
+ * each side of k (Algorithm 2, steps 4 and 7) streams Y from memory, and all
+ * other modes follow from the much smaller partial tensors R^(n), L^(n)
+ * (eqs. 3.19-3.22, steps 11, 15, 19, 20).  No mode-n unfolding is ever formed.
+ * On top of it sits the fast CP_ALS sweep of Section 4 (update rule eq. 2.14).
+ *
+ * Conventions shared by every entry point
+ *  - Tensor layout: vec(Y) with mode 1 fastest (column-major, eq. 2.1).  Y is a
+ *    DEVICE pointer to prod(I) elements.
+ *  - Modes are 0-based in this API (the paper is 1-based): n in [0, N).
+ *  - Factor A^(n) and gradient G^(n) are I_n x R column-major matrices
+ *    (leading dimension I_n), DEVICE pointers.  `A` and `G` are HOST arrays
+ *    of N such device pointers.
+ *  - Element type: double when opts->precision == CPG_FP64, float otherwise
+ *    (Y, A, G alike).  lambda and fit are always double.
+ *  - The caller owns all memory.  The library never allocates device memory:
+ *    every call takes a caller-provided device workspace of at least
+ *    cpg_workspace_size(...) bytes (opts->workspace, 256-byte aligned), whose
+ *    first 256 bytes hold the device status word (cpg_workspace_init clears it).
+ *  - Calls are asynchronous on opts->stream (a cudaStream_t; NULL = legacy
+ *    default stream).  The returned status covers argument checks and launch
+ *    errors.  Conditions found on the device (a singular normal-equation
+ *    matrix in CP_ALS, a bounded wait that expired) are recorded in a status
+ *    word inside the workspace; cpg_device_status() synchronizes the stream
+ *    and returns and clears it.
+ *  - Argument errors (return CPG_ERR_ARG): N < 2 or N > CPG_MAX_ORDER, any
+ *    I_n < 1, R < 1 or R > CPG_MAX_RANK, a NULL pointer where one is
+ *    required, a mode n out of range, split not in {0} U [1, N-1], an unknown
+ *    precision.  prod(I) overflowing int64 returns CPG_ERR_SHAPE.  A workspace
+ *    that is NULL or too small returns CPG_ERR_WORKSPACE.  A precision that
+ *    has no kernel for the call returns CPG_ERR_UNSUPPORTED.  Nothing is
+ *    launched when a call returns an error.
+ */
+#ifndef CPGRAD_H
+#define CPGRAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPG_MAX_ORDER 16
+#define CPG_MAX_RANK 256
+
+typedef enum {
+  CPG_OK = 0,
+  CPG_ERR_ARG = 1,
+  CPG_ERR_SHAPE = 2,
+  CPG_ERR_WORKSPACE = 3,
+  CPG_ERR_SINGULAR = 4,
+  CPG_ERR_CUDA = 5,
+  CPG_ERR_TIMEOUT = 6,
+  CPG_ERR_UNSUPPORTED = 7
+} cpg_status;
+
+/* Arithmetic of the leading contraction (Algorithm 2, steps 4 and 7), the
+ * part that streams Y.  Everything after it runs in FP32 (FP64 for
+ * CPG_FP64), and the CP_ALS normal equations always run in FP64. */
+typedef enum {
+  CPG_FP32 = 0,    /* FP32 CUDA-core FMA, FP32 accumulation                     */
+  CPG_TF32X3 = 1,  /* 3-term split TF32 products on tcgen05, FP32 accumulation */
+  CPG_BF16X3 = 2,  /* 3-term split BF16 products on tcgen05, FP32 accumulation */
+  CPG_BF16 = 3,    /* single BF16 product on tcgen05, FP32 accumulation        */
+  CPG_FP64 = 4     /* FP64 tensor and factors, FP64 CUDA-core FMA              */
+} cpg_precision;
+
+typedef struct {
+  int precision;          /* cpg_precision                                      */
+  int split;              /* k = number of leading modes in J; 0 = n* (Alg. 2 step 1) */
+  void* workspace;        /* device scratch, >= cpg_workspace_size() bytes       */
+  size_t workspace_bytes;
+  void* stream;           /* cudaStream_t; NULL = legacy default stream          */
+} cpg_opts;
+
+/* Which call a workspace is sized for. */
+typedef enum { CPG_CALL_GRADIENT_ALL = 0, CPG_CALL_GRADIENT_MODE = 1, CPG_CALL_ALS = 2 } cpg_call;
+
+/* n* = max{n : J_n <= K_n} of Algorithm 2 step 1, 1-based count of leading
+ * modes, clamped into [1, N-1] (when I_1 > I_2...I_N no n qualifies and 1 is
+ * returned).  Host-only; returns 0 on invalid arguments. */
+int cpg_split_point(const int64_t* I, int N);
+
+/* Bytes of device workspace that `call` needs for this shape, rank and
+ * options (opts->precision and opts->split are read; NULL opts = defaults).
+ * Host-only.  Returns 0 on invalid arguments. */
+size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call);
+
+/* All-mode CP gradient, Algorithm 2 (Section 3.3): G[n] <- Y_(n) KR_{m != n}
+ * for every n in [0, N).  One pass over Y computes both leading
+ * contractions (steps 4 and 7) from each tile; the other modes follow from
+ * R^(n) and L^(n) (steps 11, 15, 19, 20).  G[n] are overwritten. */
+cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                           void* const* G, const cpg_opts* opts);
+
+/* Single-mode CP gradient, Section 3.2: G^(n) via the right-to-left route
+ * (eqs. 3.7, 3.10, 3.12) when J_n <= K_{n-1}, else the left-to-right route
+ * (eqs. 3.8, 3.9, 3.16).  Gn (I_n x R) is overwritten. */
+cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                            int n, void* Gn, const cpg_opts* opts);
+
+/* `iters` sweeps of the fast CP_ALS of Section 4 with update rule eq. 2.14.
+ * Mode order per sweep (0-based, k = split): k-1, k-2, ..., 0, k, ..., N-1.
+ * Each update solves A^(n) V = G^(n), V = Hadamard_{m != n} A^(m)T A^(m), by
+ * FP64 Cholesky, then normalises the columns: lambda_r = ||a_r^(n)||,
+ * a_r^(n) /= lambda_r.  A[n] (device, I_n x R) and lambda (device, R
+ * doubles) are updated in place; A on entry is the starting point.
+ * fit (device, `iters` doubles, may be NULL) receives after each sweep
+ * fit = 1 - ||Y - Yhat||_F / ||Y||_F computed from R x R quantities.
+ * A V that is not positive definite leaves that mode unchanged and records
+ * CPG_ERR_SINGULAR in the device status word. */
+cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
+                       int iters, double* fit, const cpg_opts* opts);
+
+/* Clears the device status word at the start of opts->workspace (stream
+ * ordered).  Call once on a new workspace before its first use; the status
+ * word is otherwise left as the device wrote it. */
+cpg_status cpg_workspace_init(const cpg_opts* opts);
+
+/* Synchronizes opts->stream, returns the device status word recorded since the
+ * last call (CPG_OK if none) and clears it. */
+cpg_status cpg_device_status(const cpg_opts* opts);
+
+/* Static description of a status code. */
+const char* cpg_status_str(int status);
+
+/* Kernel launches issued by this library on the calling thread since the
+ * last reset (counts what the host enqueued; for benchmarks). */
+uint64_t cpg_launch_count(int reset);
+
+/* Benchmark instrumentation of the leading contraction (Algorithm 2 steps 4
+ * and 7, the kernel that streams Y).  While enabled, every leading-pass launch
+ * is bracketed by two CUDA events recorded on its own stream (at most 4096
+ * launches are kept).  enable = 1 creates the events on first use and starts
+ * a new record; 0 stops recording.  Returns CPG_OK or CPG_ERR_CUDA.
+ * Not thread-safe: one recording thread at a time. */
+int cpg_profile_lead(int enable);
+
+/* Waits for and returns the recorded launch durations in milliseconds
+ * (ms[i]) and the sides each launch computed (sides[i]: 1 = step 4 only,
+ * 2 = step 7 only, 3 = both), at most `max` entries, then clears the record.
+ * Either array may be NULL.  Returns the number of entries, or -1 on a CUDA
+ * error. */
+int cpg_profile_read(float* ms, int* sides, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPGRAD_H */

@@ -1,0 +1,9 @@
+"""GB300-native fast CP gradients and CP_ALS (Phan, Tichavsky, Cichocki).
+
+The computation lives in ``libcpgrad.so`` (CUDA, sm_103a) behind the C ABI
+of ``include/cpgrad.h``; ``cpgrad`` is its argument-marshalling binding.
+"""
+from .cpgrad import (  # noqa: F401
+    cpg_split_point, cpg_workspace_size, cp_gradient_all, cp_gradient_mode, cp_als_iter, cpg_device_status,
+    colmajor, launch_count, profile_lead, profile_read, Workspace, CpgError, PRECISIONS, lib,
+)

@@ -1,0 +1,270 @@
+"""Python binding of libcpgrad.so: argument marshalling only.
+
+Every step of the computation runs in the CUDA library behind the C ABI
+declared in ``include/cpgrad.h``; this module only checks tensor layouts,
+allocates outputs and workspace with PyTorch, and passes device pointers
+and the current CUDA stream.  There is no CPU fallback: if the library is
+missing, importing the low-level handle raises.
+
+Layouts (as in the C ABI): vec(Y) is a 1-D tensor with mode 1 fastest
+(eq. 2.1); factor A^(n) and gradient G^(n) are (I_n, R) tensors stored
+column-major (stride (1, I_n)); ``colmajor()`` converts.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpgrad.so")
+
+CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR_CUDA, CPG_ERR_TIMEOUT, \
+    CPG_ERR_UNSUPPORTED = range(8)
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4}
+CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS = 0, 1, 2
+EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
+           "cpg_workspace_init", "cpg_device_status", "cpg_status_str", "cpg_launch_count", "cpg_profile_lead",
+           "cpg_profile_read"]
+
+
+class CpgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} (status {status})")
+        self.status = status
+
+
+class cpg_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("split", ctypes.c_int), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcpgrad.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        vpp = ctypes.POINTER(ctypes.c_void_p)
+        L.cpg_split_point.argtypes = [i64p, ctypes.c_int]
+        L.cpg_split_point.restype = ctypes.c_int
+        L.cpg_workspace_size.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts), ctypes.c_int]
+        L.cpg_workspace_size.restype = ctypes.c_size_t
+        L.cp_gradient_all.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, vpp,
+                                      ctypes.POINTER(cpg_opts)]
+        L.cp_gradient_all.restype = ctypes.c_int
+        L.cp_gradient_mode.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.POINTER(cpg_opts)]
+        L.cp_gradient_mode.restype = ctypes.c_int
+        L.cp_als_iter.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cpg_opts)]
+        L.cp_als_iter.restype = ctypes.c_int
+        L.cpg_workspace_init.argtypes = [ctypes.POINTER(cpg_opts)]
+        L.cpg_workspace_init.restype = ctypes.c_int
+        L.cpg_device_status.argtypes = [ctypes.POINTER(cpg_opts)]
+        L.cpg_device_status.restype = ctypes.c_int
+        L.cpg_status_str.argtypes = [ctypes.c_int]
+        L.cpg_status_str.restype = ctypes.c_char_p
+        L.cpg_launch_count.argtypes = [ctypes.c_int]
+        L.cpg_launch_count.restype = ctypes.c_uint64
+        L.cpg_profile_lead.argtypes = [ctypes.c_int]
+        L.cpg_profile_lead.restype = ctypes.c_int
+        L.cpg_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.cpg_profile_read.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().cpg_status_str(int(status)).decode()
+
+
+def _i64(I: Sequence[int]):
+    return (ctypes.c_int64 * len(I))(*[int(v) for v in I])
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[ctypes.c_void_p(t.data_ptr()) for t in ts])
+
+
+def _prec(precision) -> int:
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def cpg_split_point(I: Sequence[int]) -> int:
+    return int(lib().cpg_split_point(_i64(I), len(I)))
+
+
+def cpg_workspace_size(I: Sequence[int], R: int, precision="fp32", split: int = 0, call: int = CALL_GRADIENT_ALL) -> int:
+    o = cpg_opts(_prec(precision), int(split), None, 0, None)
+    return int(lib().cpg_workspace_size(_i64(I), len(I), int(R), ctypes.byref(o), int(call)))
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(lib().cpg_launch_count(1 if reset else 0))
+
+
+def profile_lead(enable: bool) -> None:
+    """Start (True) or stop (False) event timing of leading-pass launches."""
+    st = lib().cpg_profile_lead(1 if enable else 0)
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_profile_lead")
+
+
+def profile_read(max_entries: int = 4096):
+    """[(milliseconds, sides)] of the leading-pass launches recorded since profile_lead(True)."""
+    ms = (ctypes.c_float * max_entries)()
+    sd = (ctypes.c_int * max_entries)()
+    n = lib().cpg_profile_read(ms, sd, max_entries)
+    if n < 0:
+        raise CpgError(CPG_ERR_CUDA, "cpg_profile_read")
+    return [(float(ms[i]), int(sd[i])) for i in range(n)]
+
+
+# ---- torch-facing helpers -------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(A):
+    """(I, R) tensor with column-major storage (stride (1, I))."""
+    return A.t().contiguous().t()
+
+
+def _check_colmajor(A, In, R, dtype, name):
+    if tuple(A.shape) != (In, R) or A.dtype != dtype or not A.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA {dtype} tensor of shape ({In}, {R}), got {tuple(A.shape)} {A.dtype}")
+    if A.numel() > 0 and not (A.stride(0) == 1 and (R == 1 or A.stride(1) == In)):
+        raise ValueError(f"{name}: must be column-major (stride (1, {In})); use colmajor()")
+
+
+class Workspace:
+    """Device scratch for the library, held as a torch uint8 tensor and grown on demand."""
+
+    def __init__(self, device=None):
+        self.buf = None
+        self.device = device
+
+    def get(self, nbytes: int, stream_ptr):
+        torch = _torch()
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device or "cuda")
+            o = cpg_opts(0, 0, ctypes.c_void_p(self.buf.data_ptr()), self.buf.numel(), ctypes.c_void_p(stream_ptr))
+            st = lib().cpg_workspace_init(ctypes.byref(o))
+            if st != CPG_OK:
+                raise CpgError(st, "cpg_workspace_init")
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _opts(precision, split, ws: Workspace, nbytes, stream_ptr):
+    buf = ws.get(nbytes, stream_ptr)
+    return cpg_opts(_prec(precision), int(split), ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                    ctypes.c_void_p(stream_ptr))
+
+
+def _ws_for(workspace, device):
+    if workspace is not None:
+        return workspace
+    key = str(device)
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(device)
+    return _default_ws[key]
+
+
+def _check_y(Y, I, dtype):
+    n = 1
+    for v in I:
+        n *= int(v)
+    if not Y.is_cuda or Y.dtype != dtype or Y.numel() != n or not Y.is_contiguous():
+        raise ValueError(f"Y: expected a contiguous CUDA {dtype} tensor with {n} elements (vec(Y), mode 1 fastest)")
+
+
+def cp_gradient_all(Y, I: Sequence[int], A, G=None, *, precision="fp32", split: int = 0, workspace=None,
+                    stream=None):
+    """All-mode CP gradient (Algorithm 2).  Returns the list of G^(n) (I_n x R, column-major)."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for n, a in enumerate(A):
+        _check_colmajor(a, int(I[n]), R, dtype, f"A[{n}]")
+    if G is None:
+        G = [torch.empty((R, int(In)), dtype=dtype, device=Y.device).t() for In in I]
+    for n, g in enumerate(G):
+        _check_colmajor(g, int(I[n]), R, dtype, f"G[{n}]")
+    sp = _stream_ptr(stream)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_GRADIENT_ALL), sp)
+    st = lib().cp_gradient_all(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, _ptrs(G), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_gradient_all")
+    return G
+
+
+def cp_gradient_mode(Y, I: Sequence[int], A, n: int, Gn=None, *, precision="fp32", workspace=None, stream=None):
+    """Single-mode CP gradient (Section 3.2)."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for m, a in enumerate(A):
+        _check_colmajor(a, int(I[m]), R, dtype, f"A[{m}]")
+    if Gn is None:
+        Gn = torch.empty((R, int(I[n])), dtype=dtype, device=Y.device).t()
+    _check_colmajor(Gn, int(I[n]), R, dtype, "Gn")
+    sp = _stream_ptr(stream)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, 0, ws, cpg_workspace_size(I, R, precision, 0, CALL_GRADIENT_MODE), sp)
+    st = lib().cp_gradient_mode(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, int(n),
+                                ctypes.c_void_p(Gn.data_ptr()), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_gradient_mode")
+    return Gn
+
+
+def cp_als_iter(Y, I: Sequence[int], A, iters: int, lam=None, fit=None, *, precision="fp32", split: int = 0,
+                workspace=None, stream=None):
+    """``iters`` fast CP_ALS sweeps (Section 4); A (list of column-major factors) is updated in place.
+    Returns (lambda, fit) as CUDA float64 tensors."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for m, a in enumerate(A):
+        _check_colmajor(a, int(I[m]), R, dtype, f"A[{m}]")
+    if lam is None:
+        lam = torch.ones(R, dtype=torch.float64, device=Y.device)
+    if fit is None:
+        fit = torch.zeros(max(int(iters), 1), dtype=torch.float64, device=Y.device)
+    sp = _stream_ptr(stream)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_ALS), sp)
+    st = lib().cp_als_iter(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), ctypes.c_void_p(lam.data_ptr()),
+                           R, int(iters), ctypes.c_void_p(fit.data_ptr()), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_als_iter")
+    return lam, fit
+
+
+def cpg_device_status(workspace=None, device=None, stream=None) -> int:
+    """Synchronize and read (and clear) the device status word of a workspace."""
+    ws = _ws_for(workspace, device or "cuda")
+    if ws.buf is None:
+        return CPG_OK
+    o = cpg_opts(0, 0, ctypes.c_void_p(ws.buf.data_ptr()), ws.buf.numel(), ctypes.c_void_p(_stream_ptr(stream)))
+    return int(lib().cpg_device_status(ctypes.byref(o)))

@@ -1,0 +1,735 @@
+// C ABI of cpgrad: argument checks, planning, workspace layout and the launch
+// sequences of Algorithm 2 (all-mode gradient), Section 3.2 (single-mode
+// gradient) and Section 4 (fast CP_ALS).
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "als.cuh"
+#include "chain.cuh"
+#include "common.cuh"
+#include "lead_dispatch.cuh"
+
+using namespace cpg;
+
+namespace {
+
+thread_local uint64_t g_launches = 0;
+
+// Optional timing of leading-pass launches: CUDA events recorded on the launch
+// stream around every leading-contraction kernel while enabled.
+struct LeadTiming {
+  bool on = false;
+  int n = 0;
+  static constexpr int kMax = 4096;
+  cudaEvent_t ev[2 * kMax] = {};
+  int sides[kMax] = {};
+  bool made = false;
+};
+LeadTiming g_timing;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      g_num_sms = n;
+    else
+      return 152;
+  }
+  return g_num_sms;
+}
+
+struct Shape {
+  int N = 0;
+  int64_t I[kMaxOrder] = {};
+  int64_t total = 0;
+};
+
+cpg_status check_shape(const int64_t* I, int N, int R, Shape& s) {
+  if (I == nullptr || N < 2 || N > kMaxOrder || R < 1 || R > CPG_MAX_RANK) return CPG_ERR_ARG;
+  s.N = N;
+  int64_t t = 1;
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1) return CPG_ERR_ARG;
+    if (t > INT64_MAX / I[n]) return CPG_ERR_SHAPE;
+    t *= I[n];
+    s.I[n] = I[n];
+  }
+  s.total = t;
+  return CPG_OK;
+}
+
+int64_t prod(const Shape& s, int b, int e) {
+  int64_t p = 1;
+  for (int m = b; m < e; ++m) p *= s.I[m];
+  return p;
+}
+
+// n* of Algorithm 2 step 1 (1-based count of leading modes), clamped to [1, N-1].
+int split_point(const Shape& s) {
+  int best = 0;
+  for (int n = 1; n <= s.N; ++n)
+    if (prod(s, 0, n) <= prod(s, n, s.N)) best = n;
+  return std::min(std::max(best, 1), s.N - 1);
+}
+
+bool is_f64(int prec) { return prec == CPG_FP64; }
+
+// ---- leading-pass plan ----------------------------------------------------------
+struct LeadPlan {
+  int k = 0, sides = 0;
+  int64_t J = 0, K = 0;
+  int RTmax = 0, groups = 0;   // rank groups of at most RTmax columns
+  int TJ = 0, TK = 0, nrt = 1;
+  int nJb = 0, nKs = 0;
+  int64_t Kc = 0;
+  size_t rpart_elems = 0, lpart_elems = 0;
+};
+
+SimtShape shape_for(int prec, int r) { return is_f64(prec) ? simt_shape_f64(r) : simt_shape_f32(r); }
+
+LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
+  LeadPlan p;
+  p.k = k;
+  p.sides = sides;
+  p.J = prod(s, 0, k);
+  p.K = prod(s, k, s.N);
+  p.RTmax = is_f64(prec) ? kMaxRankTileF64 : kMaxRankTileF32;
+  p.groups = (R + p.RTmax - 1) / p.RTmax;
+  // All rank groups share one tile geometry: the widest group's.
+  const SimtShape sh = shape_for(prec, std::min(R, p.RTmax));
+  p.TJ = sh.TJ;
+  p.TK = sh.TK;
+  if (sides == 2) {
+    // L side alone: tall J-blocks (about 2048 rows) keep the J-block partials few.
+    const int64_t tiles = (p.J + p.TJ - 1) / p.TJ;
+    p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, std::max(1, 2048 / p.TJ))));
+  } else {
+    p.nrt = 1;
+  }
+  const int64_t jrows = int64_t(p.TJ) * p.nrt;
+  p.nJb = int((p.J + jrows - 1) / jrows);
+  const int64_t chunks = (p.K + p.TK - 1) / p.TK;
+  const int slots = num_sms();  // one CTA per SM (shared-memory bound)
+  double best = -1.0;
+  int best_ks = 1;
+  const int64_t max_ks = std::min<int64_t>(chunks, 4096);
+  for (int64_t ks = 1; ks <= max_ks; ++ks) {
+    const int64_t per = (chunks + ks - 1) / ks;  // chunks per CTA
+    const int64_t nks = (chunks + per - 1) / per;
+    if (nks != ks) continue;
+    const int64_t units = int64_t(p.nJb) * nks;
+    if (units > 65535LL * 64) break;
+    const int64_t waves = (units + slots - 1) / slots;
+    const double eff = double(units) / double(waves * slots);
+    const double stages = double(per * p.nrt);
+    const double score = eff * stages / (stages + 1.5);
+    if (score > best + 1e-9) {
+      best = score;
+      best_ks = int(nks);
+    }
+  }
+  p.nKs = best_ks;
+  const int64_t per = (chunks + p.nKs - 1) / p.nKs;
+  p.Kc = per * p.TK;
+  p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
+  p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
+  return p;
+}
+
+// ---- workspace ------------------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename U>
+  U* take(size_t n) {
+    U* p = base ? reinterpret_cast<U*>(base + off) : nullptr;
+    off = align_up(off + n * sizeof(U));
+    return p;
+  }
+};
+
+struct Header {
+  int* status;
+  double* normY2;
+};
+
+Header take_header(Carver& c) {
+  Header h;
+  char* p = c.take<char>(kAlign);
+  h.status = reinterpret_cast<int*>(p);
+  h.normY2 = p ? reinterpret_cast<double*>(p + 8) : nullptr;
+  return h;
+}
+
+template <typename T>
+struct ChainBufs {
+  T* Pa = nullptr;
+  T* Pb = nullptr;
+  T* Qa = nullptr;
+  T* Qb = nullptr;
+  T* kr = nullptr;
+};
+
+int64_t kr_len_max(const Shape& s, int k) {
+  // Longest Kronecker vector the chains build: modes [0, n-1) for n <= k, or
+  // modes (n, N) for n >= k.
+  int64_t m = 1;
+  for (int n = 1; n <= k; ++n) m = std::max(m, prod(s, 0, n - 1));
+  for (int n = k; n < s.N; ++n) m = std::max(m, prod(s, n + 1, s.N));
+  return m;
+}
+
+template <typename T>
+ChainBufs<T> take_chain(Carver& c, const Shape& s, int R, int64_t J, int64_t K, int k) {
+  ChainBufs<T> b;
+  b.Pa = c.take<T>(size_t(R) * J);
+  b.Pb = c.take<T>(size_t(R) * J);
+  b.Qa = c.take<T>(size_t(R) * K);
+  b.Qb = c.take<T>(size_t(R) * K);
+  b.kr = c.take<T>(size_t(R) * kr_len_max(s, k));
+  return b;
+}
+
+struct GradLayout {
+  LeadPlan lead;
+  size_t bytes = 0;
+};
+
+template <typename T>
+struct GradWs {
+  Header h;
+  T* Rpart;
+  T* Lpart;
+  ChainBufs<T> ch;
+};
+
+template <typename T>
+GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size_t* bytes) {
+  Carver c(base);
+  GradWs<T> w;
+  w.h = take_header(c);
+  w.Rpart = c.take<T>(std::max<size_t>(lp.rpart_elems, 1));
+  w.Lpart = c.take<T>(std::max<size_t>(lp.lpart_elems, 1));
+  w.ch = take_chain<T>(c, s, R, lp.J, lp.K, lp.k);
+  if (bytes) *bytes = c.off;
+  return w;
+}
+
+// Fused pass unless its J-block partials would cost more than a fifth of Y's
+// bytes; then the two sides run as separate passes (the L pass with tall blocks).
+bool use_fused(const Shape& s, int R, int k, int prec) {
+  const LeadPlan f = plan_lead(s, R, k, 3, prec);
+  return double(f.lpart_elems + f.rpart_elems) <= 0.2 * double(s.total);
+}
+
+template <typename T>
+struct ModeWs {
+  Header h;
+  T* part;
+  T* kr;
+};
+
+struct ModeRoute {
+  bool right;
+  LeadPlan lead;
+};
+
+ModeRoute mode_route(const Shape& s, int R, int n, int prec) {
+  ModeRoute m;
+  // Section 3.2: right-to-left (eq. 3.7) when J_n <= K_{n-1} (1-based), else left-to-right.
+  m.right = prod(s, 0, n + 1) <= prod(s, n, s.N);
+  m.lead = m.right ? plan_lead(s, R, n + 1, 1, prec) : plan_lead(s, R, n, 2, prec);
+  return m;
+}
+
+template <typename T>
+ModeWs<T> carve_mode(void* base, const Shape& s, int R, int n, const ModeRoute& rt, size_t* bytes) {
+  Carver c(base);
+  ModeWs<T> w;
+  w.h = take_header(c);
+  w.part = c.take<T>(std::max<size_t>(rt.right ? rt.lead.rpart_elems : rt.lead.lpart_elems, 1));
+  const int64_t len = rt.right ? prod(s, 0, n) : prod(s, n + 1, s.N);
+  w.kr = c.take<T>(size_t(R) * len);
+  if (bytes) *bytes = c.off;
+  return w;
+}
+
+template <typename T>
+struct AlsWs {
+  Header h;
+  T* Rpart;
+  T* Lpart;
+  double* normpart;
+  ChainBufs<T> ch;
+  double* grams;
+  double* X;
+  T* G;
+};
+
+template <typename T>
+AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const LeadPlan& ll, size_t* bytes) {
+  Carver c(base);
+  AlsWs<T> w;
+  w.h = take_header(c);
+  w.Rpart = c.take<T>(std::max<size_t>(lr.rpart_elems, 1));
+  w.Lpart = c.take<T>(std::max<size_t>(ll.lpart_elems, 1));
+  w.normpart = c.take<double>(size_t(lr.nJb) * lr.nKs);
+  w.ch = take_chain<T>(c, s, R, lr.J, lr.K, lr.k);
+  int64_t imax = 1;
+  for (int n = 0; n < s.N; ++n) imax = std::max(imax, s.I[n]);
+  w.grams = c.take<double>(size_t(s.N) * R * R);
+  w.X = c.take<double>(size_t(imax) * R);
+  w.G = c.take<T>(size_t(imax) * R);
+  if (bytes) *bytes = c.off;
+  return w;
+}
+
+// ---- launches -------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_lead(const LeadArgs<T>& a, int RT, int sides, dim3 g, cudaStream_t st) {
+  ++g_launches;
+  const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
+  const int slot = g_timing.n;
+  if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 8) e = launch_lead_f64(a, RT, sides, g, st);
+  else e = launch_lead_f32(a, RT, sides, g, st);
+  if (timed) {
+    cudaEventRecord(g_timing.ev[2 * slot + 1], st);
+    g_timing.sides[slot] = sides;
+    g_timing.n = slot + 1;
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, const LeadPlan& p, T* Rpart, T* Lpart,
+                     double* normpart, int prec, cudaStream_t st) {
+  LeadArgs<T> a{};
+  a.Y = Y;
+  a.J = p.J;
+  a.K = p.K;
+  a.N = s.N;
+  a.k = p.k;
+  a.R = R;
+  for (int m = 0; m < s.N; ++m) {
+    a.I[m] = s.I[m];
+    a.A[m] = static_cast<const T*>(A[m]);
+  }
+  a.Kc = p.Kc;
+  a.nrt = p.nrt;
+  a.Rpart = Rpart;
+  a.Lpart = Lpart;
+  a.vec_ok = ((reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (p.J * int64_t(sizeof(T))) % 16 == 0) ? 1 : 0;
+  // Every rank group runs the widest group's instance; ranks beyond R are masked.
+  const int RT = shape_for(prec, std::min(R, p.RTmax)).RT;
+  for (int g = 0; g < p.groups; ++g) {
+    a.r0 = g * p.RTmax;
+    a.normpart = (g == 0) ? normpart : nullptr;
+    cudaError_t e = launch_lead(a, RT, p.sides, dim3(p.nJb, p.nKs), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+inline int blocks_for(int64_t n, int threads, int cap = 4 * 1024) {
+  int64_t b = (n + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min<int64_t>(b, cap)));
+}
+
+template <typename T>
+FacArgs<T> fac_args(const Shape& s, const void* const* A) {
+  FacArgs<T> f{};
+  for (int m = 0; m < s.N; ++m) {
+    f.I[m] = s.I[m];
+    f.A[m] = static_cast<const T*>(A[m]);
+  }
+  return f;
+}
+
+// Kronecker vector over modes [mb, me) (eq. 3.3), [r][o] layout.  For a single
+// mode it is the factor itself (column-major I x R has the same layout).
+template <typename T>
+const T* kr_vector(const Shape& s, const void* const* A, int R, int mb, int me, T* scratch, cudaStream_t st) {
+  if (me - mb <= 0) return nullptr;
+  if (me - mb == 1) return static_cast<const T*>(A[mb]);
+  const int64_t len = prod(s, mb, me);
+  ++g_launches;
+  kr_build_kernel<T><<<blocks_for(len * R, 256), 256, 0, st>>>(scratch, fac_args<T>(s, A), mb, me, len, R);
+  return scratch;
+}
+
+template <typename T, bool RIGHT>
+void launch_grad(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, int R, const T* kr, T* G, T* Xred,
+                 cudaStream_t st) {
+  const int64_t warps = In * R;
+  const int blocks = int((warps + 7) / 8);
+  ++g_launches;
+  mode_grad_kernel<T, RIGHT><<<blocks, 256, 0, st>>>(X, nparts, pstride, len_o, In, R, kr, G, Xred);
+}
+
+template <typename T, bool RIGHT>
+void launch_contract(const T* X, int64_t len_o, int64_t In, int R, const T* An, T* Xout, cudaStream_t st) {
+  ++g_launches;
+  mode_contract_kernel<T, RIGHT><<<blocks_for(len_o * R, 256), 256, 0, st>>>(X, len_o, In, R, An, Xout);
+}
+
+cpg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPG_OK : CPG_ERR_CUDA; }
+
+cpg_status common_checks(const cpg_opts* opts, Shape& s, const int64_t* I, int N, int R) {
+  if (opts == nullptr) return CPG_ERR_ARG;
+  cpg_status st = check_shape(I, N, R, s);
+  if (st != CPG_OK) return st;
+  if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
+  if (opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return CPG_ERR_ARG;
+  if (opts->precision != CPG_FP32 && opts->precision != CPG_FP64) return CPG_ERR_UNSUPPORTED;
+  return CPG_OK;
+}
+
+int choose_split(const Shape& s, const cpg_opts* opts) {
+  return (opts && opts->split != 0) ? opts->split : split_point(s);
+}
+
+// ---- all-mode gradient (Algorithm 2) ------------------------------------------------
+template <typename T>
+cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, int R, void* const* G,
+                             const cpg_opts* o) {
+  cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  const int k = choose_split(s, o);
+  const bool fused = use_fused(s, R, k, o->precision);
+  LeadPlan pr = plan_lead(s, R, k, fused ? 3 : 1, o->precision);
+  LeadPlan pl = fused ? pr : plan_lead(s, R, k, 2, o->precision);
+  // Workspace: one layout sized for the larger of the two plans.
+  LeadPlan sizing = pr;
+  sizing.lpart_elems = std::max(pr.lpart_elems, pl.lpart_elems);
+  size_t need = 0;
+  GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
+  if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+
+  // Steps 4 and 7: R^(k) and L^(k+1) from one read of Y (or two passes).
+  cudaError_t e = run_lead<T>(s, Y, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, st);
+  if (e == cudaSuccess && !fused) e = run_lead<T>(s, Y, A, R, pl, nullptr, w.Lpart, nullptr, o->precision, st);
+  if (e != cudaSuccess) return CPG_ERR_CUDA;
+
+  // Right side: modes k-1, ..., 0 (steps 5, 11, 12; finishing contraction line 19).
+  {
+    const T* X = w.Rpart;
+    int nparts = pr.nKs;
+    const int64_t pstride = int64_t(R) * pr.J;
+    T* bufs[2] = {w.ch.Pa, w.ch.Pb};
+    int cur = 0;
+    for (int n = k; n >= 1; --n) {
+      const int m = n - 1;
+      const int64_t len_o = prod(s, 0, m), In = s.I[m];
+      const T* kr = kr_vector<T>(s, A, R, 0, m, w.ch.kr, st);
+      T* Xred = (nparts > 1 && m > 0) ? bufs[cur] : nullptr;
+      launch_grad<T, true>(X, nparts, pstride, len_o, In, R, kr, static_cast<T*>(G[m]), Xred, st);
+      if (m > 0) {
+        const T* src = Xred ? Xred : X;
+        T* dst = bufs[cur ^ 1];
+        launch_contract<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), dst, st);
+        X = dst;
+        nparts = 1;
+        cur ^= 1;
+      }
+    }
+  }
+  // Left side: modes k, ..., N-1 (steps 8, 15, 16; finishing contraction line 20).
+  {
+    const T* X = w.Lpart;
+    int nparts = pl.nJb;
+    const int64_t pstride = int64_t(R) * pl.K;
+    T* bufs[2] = {w.ch.Qa, w.ch.Qb};
+    int cur = 0;
+    for (int n = k; n < s.N; ++n) {
+      const int64_t len_o = prod(s, n + 1, s.N), In = s.I[n];
+      const T* kr = kr_vector<T>(s, A, R, n + 1, s.N, w.ch.kr, st);
+      T* Xred = (nparts > 1 && n < s.N - 1) ? bufs[cur] : nullptr;
+      launch_grad<T, false>(X, nparts, pstride, len_o, In, R, kr, static_cast<T*>(G[n]), Xred, st);
+      if (n < s.N - 1) {
+        const T* src = Xred ? Xred : X;
+        T* dst = bufs[cur ^ 1];
+        launch_contract<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), dst, st);
+        X = dst;
+        nparts = 1;
+        cur ^= 1;
+      }
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// ---- single-mode gradient (Section 3.2) ----------------------------------------------
+template <typename T>
+cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, int R, int n, T* Gn,
+                              const cpg_opts* o) {
+  cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  const ModeRoute rt = mode_route(s, R, n, o->precision);
+  size_t need = 0;
+  ModeWs<T> w = carve_mode<T>(o->workspace, s, R, n, rt, &need);
+  if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  const LeadPlan& p = rt.lead;
+  if (rt.right) {
+    // R^(n) = Y_(1:n) (KR over modes > n) (eq. 3.10), then eq. 3.12.
+    if (run_lead<T>(s, Y, A, R, p, w.part, nullptr, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    const T* kr = kr_vector<T>(s, A, R, 0, n, w.kr, st);
+    launch_grad<T, true>(w.part, p.nKs, int64_t(R) * p.J, prod(s, 0, n), s.I[n], R, kr, Gn, nullptr, st);
+  } else {
+    // L^(n) = (KR over modes < n)^T Y_(1:n-1) (eq. 3.9), then eq. 3.16.
+    if (run_lead<T>(s, Y, A, R, p, nullptr, w.part, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    const T* kr = kr_vector<T>(s, A, R, n + 1, s.N, w.kr, st);
+    launch_grad<T, false>(w.part, p.nJb, int64_t(R) * p.K, prod(s, n + 1, s.N), s.I[n], R, kr, Gn, nullptr, st);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// ---- fast CP_ALS (Section 4) -------------------------------------------------------
+constexpr int kAlsMaxRank = 64;
+
+template <typename T>
+cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, int R, int iters, double* fit,
+                    const cpg_opts* o) {
+  cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
+  const int k = choose_split(s, o);
+  const LeadPlan lr = plan_lead(s, R, k, 1, o->precision);
+  const LeadPlan ll = plan_lead(s, R, k, 2, o->precision);
+  size_t need = 0;
+  AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
+  if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  const void* const* Ac = const_cast<const void* const*>(A);
+
+  ++g_launches;
+  gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
+  const size_t upd_smem = size_t(3) * R * R * sizeof(double);
+  cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
+
+  auto update = [&](int n, double* fit_out) {
+    AlsArgs<T> u{};
+    u.N = s.N;
+    u.n = n;
+    u.R = R;
+    u.In = s.I[n];
+    u.grams = w.grams;
+    u.G = w.G;
+    u.An = static_cast<T*>(A[n]);
+    u.lambda = lambda;
+    u.X = w.X;
+    u.status = w.h.status;
+    u.fit_out = fit_out;
+    u.normY2 = w.h.normY2;
+    ++g_launches;
+    als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
+  };
+
+  for (int it = 0; it < iters; ++it) {
+    // Pass 1: R^(k) with the current trailing factors (step 4).
+    double* np = (it == 0) ? w.normpart : nullptr;
+    if (run_lead<T>(s, Y, Ac, R, lr, w.Rpart, nullptr, np, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (it == 0) {
+      ++g_launches;
+      sum_norm_kernel<<<1, 256, 0, st>>>(w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
+    }
+    {
+      const T* X = w.Rpart;
+      int nparts = lr.nKs;
+      const int64_t pstride = int64_t(R) * lr.J;
+      T* bufs[2] = {w.ch.Pa, w.ch.Pb};
+      int cur = 0;
+      for (int n = k; n >= 1; --n) {
+        const int m = n - 1;
+        const int64_t len_o = prod(s, 0, m), In = s.I[m];
+        const T* kr = kr_vector<T>(s, Ac, R, 0, m, w.ch.kr, st);
+        T* Xred = (nparts > 1 && m > 0) ? bufs[cur] : nullptr;
+        launch_grad<T, true>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
+        update(m, nullptr);
+        if (m > 0) {
+          const T* src = Xred ? Xred : X;
+          T* dst = bufs[cur ^ 1];
+          launch_contract<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), dst, st);
+          X = dst;
+          nparts = 1;
+          cur ^= 1;
+        }
+      }
+    }
+    // Pass 2: L^(k+1) with the updated leading factors (step 7).
+    if (run_lead<T>(s, Y, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    {
+      const T* X = w.Lpart;
+      int nparts = ll.nJb;
+      const int64_t pstride = int64_t(R) * ll.K;
+      T* bufs[2] = {w.ch.Qa, w.ch.Qb};
+      int cur = 0;
+      for (int n = k; n < s.N; ++n) {
+        const int64_t len_o = prod(s, n + 1, s.N), In = s.I[n];
+        const T* kr = kr_vector<T>(s, Ac, R, n + 1, s.N, w.ch.kr, st);
+        T* Xred = (nparts > 1 && n < s.N - 1) ? bufs[cur] : nullptr;
+        launch_grad<T, false>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
+        update(n, (n == s.N - 1 && fit) ? fit + it : nullptr);
+        if (n < s.N - 1) {
+          const T* src = Xred ? Xred : X;
+          T* dst = bufs[cur ^ 1];
+          launch_contract<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), dst, st);
+          X = dst;
+          nparts = 1;
+          cur ^= 1;
+        }
+      }
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+bool ptrs_ok(const void* const* P, int N) {
+  if (P == nullptr) return false;
+  for (int n = 0; n < N; ++n)
+    if (P[n] == nullptr) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cpg_split_point(const int64_t* I, int N) {
+  Shape s;
+  if (check_shape(I, N, 1, s) != CPG_OK) return 0;
+  return split_point(s);
+}
+
+size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call) {
+  Shape s;
+  if (check_shape(I, N, R, s) != CPG_OK) return 0;
+  const int prec = opts ? opts->precision : CPG_FP32;
+  if (prec < CPG_FP32 || prec > CPG_FP64) return 0;
+  if (opts && opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return 0;
+  const int k = choose_split(s, opts);
+  size_t bytes = 0;
+  if (call == CPG_CALL_GRADIENT_ALL) {
+    const bool fused = use_fused(s, R, k, prec);
+    LeadPlan pr = plan_lead(s, R, k, fused ? 3 : 1, prec);
+    if (!fused) pr.lpart_elems = std::max(pr.lpart_elems, plan_lead(s, R, k, 2, prec).lpart_elems);
+    if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes);
+    else carve_grad<float>(nullptr, s, R, pr, &bytes);
+  } else if (call == CPG_CALL_GRADIENT_MODE) {
+    for (int n = 0; n < N; ++n) {
+      size_t b = 0;
+      const ModeRoute rt = mode_route(s, R, n, prec);
+      if (is_f64(prec)) carve_mode<double>(nullptr, s, R, n, rt, &b);
+      else carve_mode<float>(nullptr, s, R, n, rt, &b);
+      bytes = std::max(bytes, b);
+    }
+  } else if (call == CPG_CALL_ALS) {
+    const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
+    if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes);
+    else carve_als<float>(nullptr, s, R, lr, ll, &bytes);
+  } else {
+    return 0;
+  }
+  return bytes;
+}
+
+cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R, void* const* G,
+                           const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N))
+    return CPG_ERR_ARG;
+  if (is_f64(opts->precision)) return gradient_all_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts);
+  return gradient_all_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts);
+}
+
+cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* const* A, int R, int n, void* Gn,
+                            const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (n < 0 || n >= N || Y == nullptr || !ptrs_ok(A, N) || Gn == nullptr) return CPG_ERR_ARG;
+  if (is_f64(opts->precision))
+    return gradient_mode_impl<double>(s, static_cast<const double*>(Y), A, R, n, static_cast<double*>(Gn), opts);
+  return gradient_mode_impl<float>(s, static_cast<const float*>(Y), A, R, n, static_cast<float*>(Gn), opts);
+}
+
+cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R, int iters,
+                       double* fit, const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || lambda == nullptr || iters < 0)
+    return CPG_ERR_ARG;
+  if (iters == 0) return CPG_OK;
+  if (is_f64(opts->precision)) return als_impl<double>(s, static_cast<const double*>(Y), A, lambda, R, iters, fit, opts);
+  return als_impl<float>(s, static_cast<const float*>(Y), A, lambda, R, iters, fit, opts);
+}
+
+cpg_status cpg_workspace_init(const cpg_opts* opts) {
+  if (opts == nullptr || opts->workspace == nullptr || opts->workspace_bytes < kAlign) return CPG_ERR_ARG;
+  ++g_launches;
+  return cuda_status(cudaMemsetAsync(opts->workspace, 0, kAlign, static_cast<cudaStream_t>(opts->stream)));
+}
+
+cpg_status cpg_device_status(const cpg_opts* opts) {
+  if (opts == nullptr || opts->workspace == nullptr) return CPG_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CPG_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, opts->workspace, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CPG_ERR_CUDA;
+  const int zero = 0;
+  if (cudaMemcpy(opts->workspace, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return CPG_ERR_CUDA;
+  return static_cast<cpg_status>(v);
+}
+
+const char* cpg_status_str(int status) {
+  switch (status) {
+    case CPG_OK: return "ok";
+    case CPG_ERR_ARG: return "invalid argument";
+    case CPG_ERR_SHAPE: return "tensor size overflows int64";
+    case CPG_ERR_WORKSPACE: return "workspace missing or too small";
+    case CPG_ERR_SINGULAR: return "normal-equation matrix not positive definite";
+    case CPG_ERR_CUDA: return "CUDA launch or runtime error";
+    case CPG_ERR_TIMEOUT: return "bounded device wait expired";
+    case CPG_ERR_UNSUPPORTED: return "unsupported precision or size for this call";
+    default: return "unknown status";
+  }
+}
+
+int cpg_profile_lead(int enable) {
+  if (enable && !g_timing.made) {
+    for (int i = 0; i < 2 * LeadTiming::kMax; ++i)
+      if (cudaEventCreate(&g_timing.ev[i]) != cudaSuccess) return CPG_ERR_CUDA;
+    g_timing.made = true;
+  }
+  g_timing.on = enable != 0;
+  g_timing.n = 0;
+  return CPG_OK;
+}
+
+int cpg_profile_read(float* ms, int* sides, int max) {
+  if (!g_timing.made) return 0;
+  const int n = std::min(g_timing.n, max);
+  for (int i = 0; i < n; ++i) {
+    if (cudaEventSynchronize(g_timing.ev[2 * i + 1]) != cudaSuccess) return -1;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, g_timing.ev[2 * i], g_timing.ev[2 * i + 1]);
+    if (ms) ms[i] = t;
+    if (sides) sides[i] = g_timing.sides[i];
+  }
+  g_timing.n = 0;
+  return n;
+}
+
+uint64_t cpg_launch_count(int reset) {
+  const uint64_t v = g_launches;
+  if (reset) g_launches = 0;
+  return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,24 @@
+// Host-side selection of the leading-contraction kernel instance.
+#pragma once
+
+#include "common.cuh"
+
+namespace cpg {
+
+// Tile shapes of the CUDA-core leading contraction for a rank tile RT.
+struct SimtShape {
+  int RT, TJ, TK;
+  size_t smem;
+};
+
+// Smallest supported rank tile >= r (r <= max tile), its row tile TJ and columns per stage TK.
+SimtShape simt_shape_f32(int r);
+SimtShape simt_shape_f64(int r);
+constexpr int kMaxRankTileF32 = 64;
+constexpr int kMaxRankTileF64 = 16;
+
+// sides: 1 = R side, 2 = L side, 3 = both.  grid = (nJb, nKs).
+cudaError_t launch_lead_f32(const LeadArgs<float>& a, int RT, int sides, dim3 grid, cudaStream_t st);
+cudaError_t launch_lead_f64(const LeadArgs<double>& a, int RT, int sides, dim3 grid, cudaStream_t st);
+
+}  // namespace cpg

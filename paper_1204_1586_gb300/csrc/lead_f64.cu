@@ -1,0 +1,50 @@
+// FP64 instances of the CUDA-core leading contraction (Algorithm 2 steps 4/7).
+#include "lead_dispatch.cuh"
+#include "lead_simt.cuh"
+
+namespace cpg {
+
+namespace {
+template <int RT, int TJ, int SIDES>
+cudaError_t run(const LeadArgs<double>& a, dim3 grid, cudaStream_t st) {
+  using C = SimtCfg<double, RT, TJ>;
+  auto kern = lead_simt_kernel<double, RT, TJ, SIDES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, C::NT, C::smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int RT, int TJ>
+cudaError_t run_sides(const LeadArgs<double>& a, int sides, dim3 grid, cudaStream_t st) {
+  switch (sides) {
+    case 1: return run<RT, TJ, 1>(a, grid, st);
+    case 2: return run<RT, TJ, 2>(a, grid, st);
+    case 3: return run<RT, TJ, 3>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int RT, int TJ>
+SimtShape shape() {
+  using C = SimtCfg<double, RT, TJ>;
+  return SimtShape{RT, TJ, C::TK, C::smem_bytes};
+}
+}  // namespace
+
+SimtShape simt_shape_f64(int r) {
+  if (r <= 4) return shape<4, 128>();
+  if (r <= 8) return shape<8, 128>();
+  return shape<16, 64>();
+}
+
+cudaError_t launch_lead_f64(const LeadArgs<double>& a, int RT, int sides, dim3 grid, cudaStream_t st) {
+  switch (RT) {
+    case 4: return run_sides<4, 128>(a, sides, grid, st);
+    case 8: return run_sides<8, 128>(a, sides, grid, st);
+    case 16: return run_sides<16, 64>(a, sides, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cpg

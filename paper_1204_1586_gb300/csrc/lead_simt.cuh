@@ -1,0 +1,349 @@
+// Leading contractions of Algorithm 2 (steps 4 and 7) on CUDA cores.
+//
+// Y is viewed, without moving data, as the J x K column-major matrix
+// Y_(1:k) = reshape(Y, [J_k, K_k]) (eq. 2.3 / 2.11).  From one shared-memory
+// tile of Y this kernel can form both
+//
+//   R-side (step 4, eq. 3.10):  R^(k)[j, r] = sum_c Y[j, c] * W_R[c, r],
+//       W_R = A^(N) (.) ... (.) A^(k+1)   (Khatri-Rao over the trailing modes)
+//   L-side (step 7, eq. 3.9):   L^(k+1)[r, c] = sum_j W_L[j, r] * Y[j, c],
+//       W_L = A^(k) (.) ... (.) A^(1)     (Khatri-Rao over the leading modes)
+//
+// so that the all-mode gradient streams Y from memory once.  The Khatri-Rao
+// rows are generated per tile from the factor rows (the Kronecker build of
+// eq. 3.3 evaluated entry by entry) and never materialised in global memory.
+//
+// Work split: CTA (jb, ks) owns the J-block of nrt row tiles
+// [jb*nrt*TJ, (jb+1)*nrt*TJ) and the column range [ks*Kc, ks*Kc+Kc); stage s
+// covers column chunk s / nrt and row tile s % nrt.  The R side needs its
+// accumulators for every row of the block, so it runs with nrt = 1; the
+// L side alone may use tall blocks (nrt > 1) to cut the number of J-block
+// partials.  It streams column chunks of TK through a multi-stage
+// cp.async pipeline into an XOR-swizzled shared tile that serves both access
+// patterns without bank conflicts:
+//   R side: warp w takes columns w, w+8, ...; each lane holds RPL rows and
+//           accumulates all RT ranks over the CTA's columns in registers.
+//   L side: warp (wr, wc) takes a band of rows and TCL columns per lane and
+//           accumulates over rows; the WR row bands are summed through shared
+//           memory once per chunk.
+// Outputs are deterministic partial sums: Rpart[ks] (over K-splits) and
+// Lpart[jb] (over J-blocks), summed in a fixed order by the chain kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace cpg {
+
+template <typename T, int RT, int TJ>
+struct SimtCfg {
+  static constexpr int NT = 256;
+  static constexpr int VEC = 16 / int(sizeof(T));        // elements per 16-byte chunk
+  static constexpr int STAGE_BYTES = (TJ == 32) ? 16384 : 32768;
+  static constexpr int STAGES = (TJ == 32) ? 4 : 3;
+  static constexpr int TK = STAGE_BYTES / (TJ * int(sizeof(T)));  // columns per stage
+  static constexpr int CPC = TJ / VEC;                   // chunks per column
+  static constexpr int RPL = TJ / 32;                    // R side: rows per lane
+  static constexpr int VECR = RPL < VEC ? RPL : VEC;     // R side: elements per load
+  static constexpr int NLD = RPL / VECR;                 // R side: loads per column
+  static constexpr int CPW = TK / 8;                     // R side: columns per warp per stage
+  static constexpr int TCL = (TK >= 64 && RT <= 16) ? 2 : 1;  // L side: columns per lane
+  static constexpr int WC = TK / (32 * TCL);             // L side: column groups
+  static constexpr int WR = 8 / WC;                      // L side: row bands
+  static constexpr int ROWS_PW = TJ / WR;                // L side: rows per warp
+  static_assert(RT % VEC == 0, "rank tile must be a multiple of the vector width");
+  static_assert(WC >= 1 && 8 % WC == 0, "bad L-side warp grid");
+  static_assert(ROWS_PW % VEC == 0, "row band must hold whole chunks");
+  static_assert(8 * RT <= STAGES * TK, "R-side reduction must fit in the tile buffers");
+
+  static constexpr size_t y_elems = size_t(STAGES) * TK * TJ;
+  static constexpr size_t wr_elems = size_t(2) * TK * RT;
+  static constexpr size_t wl_elems = size_t(2) * TJ * RT;
+  static constexpr size_t red_elems = (WR > 1) ? size_t(WR) * RT * TK : 0;
+  static constexpr size_t smem_bytes = (y_elems + wr_elems + wl_elems + red_elems) * sizeof(T);
+  static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
+};
+
+// Swizzled position of element (c, j) inside one stage of the tile.
+template <int TJ, int VEC>
+__device__ __forceinline__ int tile_off(int c, int j) {
+  return c * TJ + (((j / VEC) ^ (c & 7)) * VEC) + (j % VEC);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&out)[N]) {
+  constexpr int B = int(sizeof(T)) * N;
+  if constexpr (B == 16) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const T* s = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = s[i];
+  } else if constexpr (B == 8) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    const T* s = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = s[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = p[i];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void sts_vec(T* p, const T (&in)[N]) {
+  constexpr int B = int(sizeof(T)) * N;
+  if constexpr (B == 16) {
+    uint4 v;
+    T* d = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = in[i];
+    *reinterpret_cast<uint4*>(p) = v;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = in[i];
+  }
+}
+
+// SIDES: bit 0 = R side (step 4), bit 1 = L side (step 7).
+template <typename T, int RT, int TJ, int SIDES>
+__global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) {
+  using C = SimtCfg<T, RT, TJ>;
+  constexpr bool DO_R = (SIDES & 1) != 0;
+  constexpr bool DO_L = (SIDES & 2) != 0;
+  constexpr int NT = C::NT, VEC = C::VEC, TK = C::TK, STAGES = C::STAGES;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ys = reinterpret_cast<T*>(smem_raw);
+  T* WRs = Ys + C::y_elems;
+  T* WLs = WRs + C::wr_elems;
+  T* red = WLs + C::wl_elems;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t J = a.J, K = a.K;
+  const int R = a.R, r0 = a.r0;
+  const int nrt = DO_R ? 1 : a.nrt;                 // row tiles per J-block
+  const int jb = blockIdx.x, ks = blockIdx.y;
+  const int64_t jblk = int64_t(jb) * TJ * nrt;      // first row of the J-block
+  const int64_t kbeg = int64_t(ks) * a.Kc;
+  const int64_t kend = (kbeg + a.Kc < K) ? (kbeg + a.Kc) : K;
+  const int nchunk = int((kend - kbeg + TK - 1) / TK);
+  const int nst = nchunk * nrt;
+  const bool do_norm = DO_R && (a.normpart != nullptr);
+
+  // Skipped (out-of-range) tile entries must read as finite values: zero once.
+  for (size_t f = tid; f < C::y_elems; f += NT) Ys[f] = T(0);
+
+  const uint64_t pol = make_evict_first_policy();
+  auto issue = [&](int it) {
+    if (it < nst) {
+      T* dst = Ys + size_t(it % STAGES) * TK * TJ;
+      const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
+      const int64_t j0 = jblk + int64_t(it % nrt) * TJ;
+      if (a.vec_ok) {
+        for (int f = tid; f < TK * C::CPC; f += NT) {
+          const int c = f / C::CPC, q = f % C::CPC;
+          const int64_t cg = cbase + c, jg = j0 + int64_t(q) * VEC;
+          if (cg < kend && jg < J) cp_async16_ef(dst + c * TJ + ((q ^ (c & 7)) * VEC), a.Y + jg + J * cg, pol);
+        }
+      } else {
+        for (int f = tid; f < TK * TJ; f += NT) {
+          const int c = f / TJ, j = f % TJ;
+          const int64_t cg = cbase + c, jg = j0 + j;
+          if (cg < kend && jg < J) cp_async_small<int(sizeof(T))>(dst + tile_off<TJ, VEC>(c, j), a.Y + jg + J * cg);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // W_L rows of row tile `rt` (Khatri-Rao over modes [0, k)).
+  auto gen_wl = [&](T* dst, int rt) {
+    const int64_t j0 = jblk + int64_t(rt) * TJ;
+    for (int f = tid; f < TJ * RT; f += NT) {
+      const int j = f / RT, r = f % RT;
+      const int64_t jg = j0 + j;
+      dst[f] = (jg < J && r0 + r < R) ? kr_entry<T>(a.A, a.I, 0, a.k, jg, r0 + r) : T(0);
+    }
+  };
+  if constexpr (DO_L) {
+    if (nrt == 1) gen_wl(WLs, 0);
+  }
+  __syncthreads();
+
+  T racc[C::NLD][C::VECR][RT];
+  T lacc[C::TCL][RT];
+  double ss = 0.0;
+  if constexpr (DO_R) {
+#pragma unroll
+    for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+      for (int e = 0; e < C::VECR; ++e)
+#pragma unroll
+        for (int r = 0; r < RT; ++r) racc[m][e][r] = T(0);
+  }
+  if constexpr (DO_L) {
+#pragma unroll
+    for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+      for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
+  }
+
+  // L-side lane placement.
+  const int wr = warp % C::WR, wc = warp / C::WR;
+  const int cl0 = wc * 32 * C::TCL + lane;
+
+#pragma unroll 1
+  for (int s = 0; s < STAGES - 1; ++s) issue(s);
+
+#pragma unroll 1
+  for (int it = 0; it < nst; ++it) {
+    cp_async_wait<STAGES - 2>();
+    const int ci = it / nrt, rt = it % nrt;
+    const int64_t cbase = kbeg + int64_t(ci) * TK;
+    if constexpr (DO_R) {
+      T* Wr = WRs + size_t(it & 1) * TK * RT;
+      for (int f = tid; f < TK * RT; f += NT) {
+        const int c = f / RT, r = f % RT;
+        const int64_t cg = cbase + c;
+        Wr[f] = (cg < kend && r0 + r < R) ? kr_entry<T>(a.A, a.I, a.k, a.N, cg, r0 + r) : T(0);
+      }
+    }
+    if constexpr (DO_L) {
+      if (nrt > 1) gen_wl(WLs + size_t(it & 1) * TJ * RT, rt);
+    }
+    __syncthreads();
+    issue(it + STAGES - 1);
+
+    const T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
+    if constexpr (DO_R) {
+      const T* Wr = WRs + size_t(it & 1) * TK * RT;
+#pragma unroll 2
+      for (int i = 0; i < C::CPW; ++i) {
+        const int c = warp + 8 * i;
+        if (cbase + c < kend) {
+          T y[C::NLD][C::VECR];
+#pragma unroll
+          for (int m = 0; m < C::NLD; ++m) {
+            const int j = lane * C::VECR + 32 * C::VECR * m;
+            lds_vec<T, C::VECR>(Yst + tile_off<TJ, VEC>(c, j), y[m]);
+          }
+#pragma unroll
+          for (int r4 = 0; r4 < RT; r4 += VEC) {
+            T w[VEC];
+            lds_vec<T, VEC>(Wr + c * RT + r4, w);
+#pragma unroll
+            for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+              for (int e = 0; e < C::VECR; ++e)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) racc[m][e][r4 + v] = fma(y[m][e], w[v], racc[m][e][r4 + v]);
+          }
+          if (do_norm) {
+#pragma unroll
+            for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+              for (int e = 0; e < C::VECR; ++e) ss += double(y[m][e]) * double(y[m][e]);
+          }
+        }
+      }
+    }
+
+    if constexpr (DO_L) {
+      const T* Wl = WLs + ((nrt > 1) ? size_t(it & 1) * TJ * RT : 0);
+#pragma unroll 2
+      for (int q = 0; q < C::ROWS_PW / VEC; ++q) {
+        const int jl = wr * C::ROWS_PW + q * VEC;
+        const int qc = jl / VEC;
+        T y[C::TCL][VEC];
+#pragma unroll
+        for (int t = 0; t < C::TCL; ++t) {
+          const int c = cl0 + 32 * t;
+          lds_vec<T, VEC>(Yst + c * TJ + ((qc ^ (c & 7)) * VEC), y[t]);
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+#pragma unroll
+          for (int r4 = 0; r4 < RT; r4 += VEC) {
+            T w[VEC];
+            lds_vec<T, VEC>(Wl + (jl + e) * RT + r4, w);
+#pragma unroll
+            for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) lacc[t][r4 + v] = fma(y[t][e], w[v], lacc[t][r4 + v]);
+          }
+        }
+      }
+      if (rt == nrt - 1) {
+        // The chunk's columns are complete over this J-block: sum the row bands.
+        if constexpr (C::WR > 1) {
+#pragma unroll
+          for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+            for (int r = 0; r < RT; ++r) red[(size_t(wr) * RT + r) * TK + cl0 + 32 * t] = lacc[t][r];
+          __syncthreads();
+          for (int f = tid; f < RT * TK; f += NT) {
+            const int r = f / TK, c = f % TK;
+            T sum = T(0);
+#pragma unroll
+            for (int w = 0; w < C::WR; ++w) sum += red[(size_t(w) * RT + r) * TK + c];
+            const int64_t cg = cbase + c;
+            if (r0 + r < R && cg < kend) a.Lpart[(int64_t(jb) * R + r0 + r) * K + cg] = sum;
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < C::TCL; ++t) {
+            const int64_t cg = cbase + cl0 + 32 * t;
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+              if (r0 + r < R && cg < kend) a.Lpart[(int64_t(jb) * R + r0 + r) * K + cg] = lacc[t][r];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+          for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
+      }
+    }
+  }
+
+  cp_async_wait<0>();
+  __syncthreads();
+
+  if constexpr (DO_R) {
+    // Sum the 8 warps' column-split partials through the (now idle) tile buffers.
+    T* redR = Ys;
+#pragma unroll
+    for (int m = 0; m < C::NLD; ++m) {
+      const int j = lane * C::VECR + 32 * C::VECR * m;
+#pragma unroll
+      for (int r = 0; r < RT; ++r) {
+        T v[C::VECR];
+#pragma unroll
+        for (int e = 0; e < C::VECR; ++e) v[e] = racc[m][e][r];
+        sts_vec<T, C::VECR>(redR + (size_t(warp) * RT + r) * TJ + j, v);
+      }
+    }
+    __syncthreads();
+    for (int f = tid; f < RT * TJ; f += NT) {
+      const int r = f / TJ, j = f % TJ;
+      T sum = T(0);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) sum += redR[(size_t(w) * RT + r) * TJ + j];
+      const int64_t jg = jblk + j;
+      if (r0 + r < R && jg < J) a.Rpart[(int64_t(ks) * R + r0 + r) * J + jg] = sum;
+    }
+    if (do_norm) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      __syncthreads();
+      double* wsum = reinterpret_cast<double*>(smem_raw);
+      if (lane == 0) wsum[warp] = ss;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += wsum[w];
+        a.normpart[int64_t(ks) * gridDim.x + jb] = t;
+      }
+    }
+  }
+}
+
+}  // namespace cpg

@@ -1,0 +1,115 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every
+symbol include/cpgrad.h declares, and its host-only logic (split point of
+Algorithm 2 step 1, workspace sizing, argument errors) behaves as documented.
+No compute entry point reaches the GPU here: every call below returns during
+argument checking."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_1204_1586_gb300 import cpgrad
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(cpgrad.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return cpgrad.lib()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "cpgrad.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) - {"defined"})
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert {"cp_gradient_all", "cp_gradient_mode", "cp_als_iter"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/cpgrad.h but not exported"
+    assert set(cpgrad.EXPORTS) <= set(names)
+
+
+@pytest.mark.parametrize("I", [[100] * 4, [60] * 5, [15] * 7, [30, 40, 50], [100, 2], [2, 100], [2, 2], [1, 1, 1],
+                               [3, 4, 5, 6, 7], [7, 6, 5, 4, 3], [1, 9, 1, 9], [64, 8, 8, 8, 8]])
+def test_split_point_matches_oracle(L, I):
+    assert cpgrad.cpg_split_point(I) == oracle.split_point(I)
+
+
+def test_split_point_invalid(L):
+    assert cpgrad.cpg_split_point([5]) == 0
+    assert cpgrad.cpg_split_point([3, 0, 2]) == 0
+
+
+def test_workspace_size(L):
+    for call in (cpgrad.CALL_GRADIENT_ALL, cpgrad.CALL_GRADIENT_MODE, cpgrad.CALL_ALS):
+        assert cpgrad.cpg_workspace_size([30, 40, 50], 5, "fp64", 0, call) > 0
+        assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, call) > 0
+        assert cpgrad.cpg_workspace_size([100] * 4, 0, "fp32", 0, call) == 0
+        assert cpgrad.cpg_workspace_size([100] * 4, 10, 9, 0, call) == 0
+        assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 4, call) == 0
+    assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, 7) == 0
+    # scratch stays well under the tensor's own size (4e8 bytes)
+    a = cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
+    b = cpgrad.cpg_workspace_size([100] * 4, 20, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
+    assert 0 < a < 4e8 and 0 < b < 4e8
+
+
+def _opts(prec=0, split=0, ws=None, nbytes=0):
+    return cpgrad.cpg_opts(prec, split, ws, nbytes, None)
+
+
+def test_argument_errors_return_before_any_launch(L):
+    I = cpgrad._i64([4, 5, 6])
+    dummy = ctypes.c_void_p(16)
+    A = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    G = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    o = _opts()
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cp_gradient_all(dummy, I, 1, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG       # N < 2
+    assert L.cp_gradient_all(dummy, I, 3, A, 0, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG       # R < 1
+    assert L.cp_gradient_all(dummy, I, 3, A, 300, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG     # R > max
+    assert L.cp_gradient_all(None, I, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG        # null Y
+    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, None) == cpgrad.CPG_ERR_ARG                  # null opts
+    bad = (ctypes.c_void_p * 3)(dummy, None, dummy)
+    assert L.cp_gradient_all(dummy, I, 3, bad, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG     # null factor
+    o9 = _opts(prec=9)
+    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(o9)) == cpgrad.CPG_ERR_ARG      # bad precision
+    o5 = _opts(split=3)
+    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(o5)) == cpgrad.CPG_ERR_ARG      # split = N
+    Ib = cpgrad._i64([4, -1, 6])
+    assert L.cp_gradient_all(dummy, Ib, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG      # I_n < 1
+    Ih = cpgrad._i64([1 << 40, 1 << 40, 1 << 40])
+    assert L.cp_gradient_all(dummy, Ih, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_SHAPE    # overflow
+    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE  # no workspace
+    small = _opts(ws=dummy, nbytes=64)
+    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(small)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_gradient_mode(dummy, I, 3, A, 3, 3, dummy, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG  # n = N
+    assert L.cp_gradient_mode(dummy, I, 3, A, 3, -1, dummy, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_gradient_mode(dummy, I, 3, A, 3, 1, None, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    lam = ctypes.c_void_p(32)
+    assert L.cp_als_iter(dummy, I, 3, A, lam, 3, -1, None, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_als_iter(dummy, I, 3, A, None, 3, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_als_iter(dummy, I, 3, A, lam, 3, 0, None, ctypes.byref(o)) == cpgrad.CPG_OK     # nothing to do
+    assert L.cp_als_iter(dummy, I, 3, A, lam, 3, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_als_iter(dummy, I, 3, A, lam, 65, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_UNSUPPORTED
+    for prec in (1, 2, 3):   # tensor-core forms are not wired into this entry point yet
+        op = _opts(prec=prec)
+        assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(op)) == cpgrad.CPG_ERR_UNSUPPORTED
+    assert cpgrad.launch_count() == n0 * 0  # nothing was launched
+    assert L.cpg_workspace_init(None) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_device_status(None) == cpgrad.CPG_ERR_ARG
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert cpgrad.status_str(s)
+    assert cpgrad.status_str(99) == "unknown status"
