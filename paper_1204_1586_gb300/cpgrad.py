@@ -177,12 +177,21 @@ def _opts(precision, split, ws: Workspace, nbytes, stream_ptr):
                     ctypes.c_void_p(stream_ptr))
 
 
+def _dev_key(device):
+    torch = _torch()
+    d = torch.device(device) if device is not None else torch.device("cuda")
+    if d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return d
+
+
 def _ws_for(workspace, device):
     if workspace is not None:
         return workspace
-    key = str(device)
+    d = _dev_key(device)
+    key = str(d)
     if key not in _default_ws:
-        _default_ws[key] = Workspace(device)
+        _default_ws[key] = Workspace(d)
     return _default_ws[key]
 
 
@@ -263,7 +272,7 @@ def cp_als_iter(Y, I: Sequence[int], A, iters: int, lam=None, fit=None, *, preci
 
 def cpg_device_status(workspace=None, device=None, stream=None) -> int:
     """Synchronize and read (and clear) the device status word of a workspace."""
-    ws = _ws_for(workspace, device or "cuda")
+    ws = _ws_for(workspace, device)
     if ws.buf is None:
         return CPG_OK
     o = cpg_opts(0, 0, ctypes.c_void_p(ws.buf.data_ptr()), ws.buf.numel(), ctypes.c_void_p(_stream_ptr(stream)))

@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
   // Skipped (out-of-range) tile entries must read as finite values: zero once.
   for (size_t f = tid; f < C::y_elems; f += NT) Ys[f] = T(0);
 
-  const uint64_t pol = make_evict_first_policy();
   auto issue = [&](int it) {
     if (it < nst) {
       T* dst = Ys + size_t(it % STAGES) * TK * TJ;
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
         for (int f = tid; f < TK * C::CPC; f += NT) {
           const int c = f / C::CPC, q = f % C::CPC;
           const int64_t cg = cbase + c, jg = j0 + int64_t(q) * VEC;
-          if (cg < kend && jg < J) cp_async16_ef(dst + c * TJ + ((q ^ (c & 7)) * VEC), a.Y + jg + J * cg, pol);
+          if (cg < kend && jg < J) cp_async16(dst + c * TJ + ((q ^ (c & 7)) * VEC), a.Y + jg + J * cg);
         }
       } else {
         for (int f = tid; f < TK * TJ; f += NT) {
