@@ -114,7 +114,8 @@ LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
   const int64_t jrows = int64_t(p.TJ) * p.nrt;
   p.nJb = int((p.J + jrows - 1) / jrows);
   const int64_t chunks = (p.K + p.TK - 1) / p.TK;
-  const int slots = num_sms();  // one CTA per SM (shared-memory bound)
+  const int bps = is_f64(prec) ? lead_blocks_per_sm_f64(sh.RT, sides) : lead_blocks_per_sm_f32(sh.RT, sides);
+  const int slots = num_sms() * std::max(bps, 1);
   double best = -1.0;
   int best_ks = 1;
   const int64_t max_ks = std::min<int64_t>(chunks, 4096);
@@ -176,6 +177,22 @@ struct ChainBufs {
   T* kr = nullptr;
 };
 
+// Kronecker tables of the leading pass's Khatri-Rao rows (modes (0, k) for
+// W_L and (k, N) for W_R; only needed when a run has three or more modes).
+template <typename T>
+struct LeadTabs {
+  T* qL = nullptr;
+  T* qR = nullptr;
+};
+
+template <typename T>
+LeadTabs<T> take_tabs(Carver& c, const Shape& s, int R, int k) {
+  LeadTabs<T> t;
+  t.qL = c.take<T>(size_t(R) * (k >= 3 ? prod(s, 1, k) : 1));
+  t.qR = c.take<T>(size_t(R) * (s.N - k >= 3 ? prod(s, k + 1, s.N) : 1));
+  return t;
+}
+
 int64_t kr_len_max(const Shape& s, int k) {
   // Longest Kronecker vector the chains build: modes [0, n-1) for n <= k, or
   // modes (n, N) for n >= k.
@@ -207,6 +224,7 @@ struct GradWs {
   T* Rpart;
   T* Lpart;
   ChainBufs<T> ch;
+  LeadTabs<T> tabs;
 };
 
 template <typename T>
@@ -217,6 +235,7 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
   w.Rpart = c.take<T>(std::max<size_t>(lp.rpart_elems, 1));
   w.Lpart = c.take<T>(std::max<size_t>(lp.lpart_elems, 1));
   w.ch = take_chain<T>(c, s, R, lp.J, lp.K, lp.k);
+  w.tabs = take_tabs<T>(c, s, R, lp.k);
   if (bytes) *bytes = c.off;
   return w;
 }
@@ -233,6 +252,7 @@ struct ModeWs {
   Header h;
   T* part;
   T* kr;
+  LeadTabs<T> tabs;
 };
 
 struct ModeRoute {
@@ -256,6 +276,7 @@ ModeWs<T> carve_mode(void* base, const Shape& s, int R, int n, const ModeRoute& 
   w.part = c.take<T>(std::max<size_t>(rt.right ? rt.lead.rpart_elems : rt.lead.lpart_elems, 1));
   const int64_t len = rt.right ? prod(s, 0, n) : prod(s, n + 1, s.N);
   w.kr = c.take<T>(size_t(R) * len);
+  w.tabs = take_tabs<T>(c, s, R, rt.lead.k);
   if (bytes) *bytes = c.off;
   return w;
 }
@@ -270,6 +291,7 @@ struct AlsWs {
   double* grams;
   double* X;
   T* G;
+  LeadTabs<T> tabs;
 };
 
 template <typename T>
@@ -286,56 +308,9 @@ AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const 
   w.grams = c.take<double>(size_t(s.N) * R * R);
   w.X = c.take<double>(size_t(imax) * R);
   w.G = c.take<T>(size_t(imax) * R);
+  w.tabs = take_tabs<T>(c, s, R, lr.k);
   if (bytes) *bytes = c.off;
   return w;
-}
-
-// ---- launches -------------------------------------------------------------------
-template <typename T>
-cudaError_t launch_lead(const LeadArgs<T>& a, int RT, int sides, dim3 g, cudaStream_t st) {
-  ++g_launches;
-  const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
-  const int slot = g_timing.n;
-  if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
-  cudaError_t e;
-  if constexpr (sizeof(T) == 8) e = launch_lead_f64(a, RT, sides, g, st);
-  else e = launch_lead_f32(a, RT, sides, g, st);
-  if (timed) {
-    cudaEventRecord(g_timing.ev[2 * slot + 1], st);
-    g_timing.sides[slot] = sides;
-    g_timing.n = slot + 1;
-  }
-  return e;
-}
-
-template <typename T>
-cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, const LeadPlan& p, T* Rpart, T* Lpart,
-                     double* normpart, int prec, cudaStream_t st) {
-  LeadArgs<T> a{};
-  a.Y = Y;
-  a.J = p.J;
-  a.K = p.K;
-  a.N = s.N;
-  a.k = p.k;
-  a.R = R;
-  for (int m = 0; m < s.N; ++m) {
-    a.I[m] = s.I[m];
-    a.A[m] = static_cast<const T*>(A[m]);
-  }
-  a.Kc = p.Kc;
-  a.nrt = p.nrt;
-  a.Rpart = Rpart;
-  a.Lpart = Lpart;
-  a.vec_ok = ((reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (p.J * int64_t(sizeof(T))) % 16 == 0) ? 1 : 0;
-  // Every rank group runs the widest group's instance; ranks beyond R are masked.
-  const int RT = shape_for(prec, std::min(R, p.RTmax)).RT;
-  for (int g = 0; g < p.groups; ++g) {
-    a.r0 = g * p.RTmax;
-    a.normpart = (g == 0) ? normpart : nullptr;
-    cudaError_t e = launch_lead(a, RT, p.sides, dim3(p.nJb, p.nKs), st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
 }
 
 inline int blocks_for(int64_t n, int threads, int cap = 4 * 1024) {
@@ -365,19 +340,117 @@ const T* kr_vector(const Shape& s, const void* const* A, int R, int mb, int me, 
   return scratch;
 }
 
+// ---- launches -------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_lead(const LeadArgs<T>& a, int RT, int sides, dim3 g, cudaStream_t st) {
+  ++g_launches;
+  const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
+  const int slot = g_timing.n;
+  if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 8) e = launch_lead_f64(a, RT, sides, g, st);
+  else e = launch_lead_f32(a, RT, sides, g, st);
+  if (timed) {
+    cudaEventRecord(g_timing.ev[2 * slot + 1], st);
+    g_timing.sides[slot] = sides;
+    g_timing.n = slot + 1;
+  }
+  return e;
+}
+
+// Khatri-Rao rows over modes [mb, me) as factor row x Kronecker-table entry.
+template <typename T>
+KrRows<T> make_rows(const Shape& s, const void* const* A, int R, int mb, int me, T* tab, cudaStream_t st) {
+  KrRows<T> w;
+  if (me <= mb) return w;
+  w.A = static_cast<const T*>(A[mb]);
+  w.d = FastDiv::make(uint32_t(s.I[mb]));
+  w.Q = kr_vector<T>(s, A, R, mb + 1, me, tab, st);
+  w.ldq = prod(s, mb + 1, me);
+  return w;
+}
+
+template <typename T>
+cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, const LeadPlan& p, T* Rpart, T* Lpart,
+                     double* normpart, int prec, const LeadTabs<T>& tabs, cudaStream_t st) {
+  LeadArgs<T> a{};
+  a.Y = Y;
+  a.J = p.J;
+  a.K = p.K;
+  a.R = R;
+  if (p.sides & 2) a.wl = make_rows<T>(s, A, R, 0, p.k, tabs.qL, st);
+  if (p.sides & 1) a.wr = make_rows<T>(s, A, R, p.k, s.N, tabs.qR, st);
+  a.Kc = p.Kc;
+  a.nrt = p.nrt;
+  a.Rpart = Rpart;
+  a.Lpart = Lpart;
+  a.vec_ok = ((reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (p.J * int64_t(sizeof(T))) % 16 == 0) ? 1 : 0;
+  // Every rank group runs the widest group's instance; ranks beyond R are masked.
+  const int RT = shape_for(prec, std::min(R, p.RTmax)).RT;
+  for (int g = 0; g < p.groups; ++g) {
+    a.r0 = g * p.RTmax;
+    a.normpart = (g == 0) ? normpart : nullptr;
+    cudaError_t e = launch_lead(a, RT, p.sides, dim3(p.nJb, p.nKs), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+void launch_seg(const SegDot<T>& p, cudaStream_t st) {
+  ++g_launches;
+  const int64_t nout = p.D * p.R;
+  auto go = [&](auto kern, int lpo) {
+    const int64_t threads = nout * lpo;
+    const int blocks = int(std::max<int64_t>(1, (threads + 255) / 256));
+    kern<<<blocks, 256, 0, st>>>(p);
+  };
+  if (p.inner >= 96) go(seg_dot_kernel<T, 32>, 32);
+  else if (p.inner >= 24) go(seg_dot_kernel<T, 8>, 8);
+  else if (p.inner >= 4) go(seg_dot_kernel<T, 4>, 4);
+  else go(seg_dot_kernel<T, 1>, 1);
+}
+
+// Finishing contraction for mode i of X (RIGHT: flat = o + len_o*i, LEFT: flat = i + In*o):
+// G[i + In r] = sum_o X[r][flat] kr[r][o].
 template <typename T, bool RIGHT>
 void launch_grad(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, int R, const T* kr, T* G, T* Xred,
                  cudaStream_t st) {
-  const int64_t warps = In * R;
-  const int blocks = int((warps + 7) / 8);
-  ++g_launches;
-  mode_grad_kernel<T, RIGHT><<<blocks, 256, 0, st>>>(X, nparts, pstride, len_o, In, R, kr, G, Xred);
+  SegDot<T> p{};
+  p.X = X;
+  p.nparts = nparts;
+  p.part_stride = pstride;
+  p.S = len_o * In;
+  p.D = In;
+  p.astep = RIGHT ? len_o : 1;
+  p.ustep = RIGHT ? 1 : In;
+  p.inner = len_o;
+  p.w = kr;
+  p.wlen = len_o;
+  p.out = G;
+  p.Xred = (nparts > 1) ? Xred : nullptr;
+  p.R = R;
+  launch_seg(p, st);
 }
 
+// Recursion over mode i of X: Xout[r][o] = sum_i X[r][flat] A[i + In r].
 template <typename T, bool RIGHT>
 void launch_contract(const T* X, int64_t len_o, int64_t In, int R, const T* An, T* Xout, cudaStream_t st) {
-  ++g_launches;
-  mode_contract_kernel<T, RIGHT><<<blocks_for(len_o * R, 256), 256, 0, st>>>(X, len_o, In, R, An, Xout);
+  SegDot<T> p{};
+  p.X = X;
+  p.nparts = 1;
+  p.part_stride = 0;
+  p.S = len_o * In;
+  p.D = len_o;
+  p.astep = RIGHT ? 1 : In;
+  p.ustep = RIGHT ? len_o : 1;
+  p.inner = In;
+  p.w = An;
+  p.wlen = In;
+  p.out = Xout;
+  p.Xred = nullptr;
+  p.R = R;
+  launch_seg(p, st);
 }
 
 cpg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPG_OK : CPG_ERR_CUDA; }
@@ -391,6 +464,9 @@ cpg_status common_checks(const cpg_opts* opts, Shape& s, const int64_t* I, int N
   if (opts->precision != CPG_FP32 && opts->precision != CPG_FP64) return CPG_ERR_UNSUPPORTED;
   return CPG_OK;
 }
+
+// The leading kernels index rows and columns with 32-bit arithmetic.
+bool lead_fits(const LeadPlan& p) { return p.J < (int64_t(1) << 31) && p.K < (int64_t(1) << 31); }
 
 int choose_split(const Shape& s, const cpg_opts* opts) {
   return (opts && opts->split != 0) ? opts->split : split_point(s);
@@ -410,11 +486,12 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   sizing.lpart_elems = std::max(pr.lpart_elems, pl.lpart_elems);
   size_t need = 0;
   GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
+  if (!lead_fits(pr) || !lead_fits(pl)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
 
   // Steps 4 and 7: R^(k) and L^(k+1) from one read of Y (or two passes).
-  cudaError_t e = run_lead<T>(s, Y, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, st);
-  if (e == cudaSuccess && !fused) e = run_lead<T>(s, Y, A, R, pl, nullptr, w.Lpart, nullptr, o->precision, st);
+  cudaError_t e = run_lead<T>(s, Y, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, w.tabs, st);
+  if (e == cudaSuccess && !fused) e = run_lead<T>(s, Y, A, R, pl, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st);
   if (e != cudaSuccess) return CPG_ERR_CUDA;
 
   // Right side: modes k-1, ..., 0 (steps 5, 11, 12; finishing contraction line 19).
@@ -473,16 +550,17 @@ cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, 
   const ModeRoute rt = mode_route(s, R, n, o->precision);
   size_t need = 0;
   ModeWs<T> w = carve_mode<T>(o->workspace, s, R, n, rt, &need);
+  if (!lead_fits(rt.lead)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
   const LeadPlan& p = rt.lead;
   if (rt.right) {
     // R^(n) = Y_(1:n) (KR over modes > n) (eq. 3.10), then eq. 3.12.
-    if (run_lead<T>(s, Y, A, R, p, w.part, nullptr, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Y, A, R, p, w.part, nullptr, nullptr, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     const T* kr = kr_vector<T>(s, A, R, 0, n, w.kr, st);
     launch_grad<T, true>(w.part, p.nKs, int64_t(R) * p.J, prod(s, 0, n), s.I[n], R, kr, Gn, nullptr, st);
   } else {
     // L^(n) = (KR over modes < n)^T Y_(1:n-1) (eq. 3.9), then eq. 3.16.
-    if (run_lead<T>(s, Y, A, R, p, nullptr, w.part, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Y, A, R, p, nullptr, w.part, nullptr, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     const T* kr = kr_vector<T>(s, A, R, n + 1, s.N, w.kr, st);
     launch_grad<T, false>(w.part, p.nJb, int64_t(R) * p.K, prod(s, n + 1, s.N), s.I[n], R, kr, Gn, nullptr, st);
   }
@@ -502,6 +580,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   const LeadPlan ll = plan_lead(s, R, k, 2, o->precision);
   size_t need = 0;
   AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
+  if (!lead_fits(lr) || !lead_fits(ll)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
   const void* const* Ac = const_cast<const void* const*>(A);
 
@@ -531,7 +610,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   for (int it = 0; it < iters; ++it) {
     // Pass 1: R^(k) with the current trailing factors (step 4).
     double* np = (it == 0) ? w.normpart : nullptr;
-    if (run_lead<T>(s, Y, Ac, R, lr, w.Rpart, nullptr, np, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Y, Ac, R, lr, w.Rpart, nullptr, np, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     if (it == 0) {
       ++g_launches;
       sum_norm_kernel<<<1, 256, 0, st>>>(w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
@@ -560,7 +639,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       }
     }
     // Pass 2: L^(k+1) with the updated leading factors (step 7).
-    if (run_lead<T>(s, Y, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Y, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     {
       const T* X = w.Lpart;
       int nparts = ll.nJb;

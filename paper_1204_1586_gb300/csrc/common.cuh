@@ -10,21 +10,56 @@ namespace cpg {
 
 constexpr int kMaxOrder = CPG_MAX_ORDER;
 
-// Device status word values (stored in the first word of the workspace).
-constexpr int kStatusOk = 0;
+// Unsigned division by a runtime constant d >= 1 for numerators below 2^31
+// (round-up multiply-and-shift method of Granlund and Montgomery, PLDI 1994):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l.  The sum fits 32 bits because n < 2^31.
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+  static FastDiv make(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    f.l = l;
+    f.m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    return f;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> l; }
+};
+
+// Khatri-Rao rows over a contiguous run of modes [mb, me) (Notation 2.1), as
+// the product of the first mode's factor and a table of the remaining modes:
+//   W[idx, r] = A_mb[idx % I_mb, r] * Q[idx / I_mb, r]
+// with Q the Kronecker table of modes (mb, me) in [r][o] layout (ld = ldq), or
+// no table when the run has a single mode, or W = 1 when the run is empty.
+template <typename T>
+struct KrRows {
+  const T* A = nullptr;   // first mode's factor, column-major (ld = d.d); nullptr: empty run
+  const T* Q = nullptr;   // table of the other modes, [r][o]; nullptr: single mode
+  int64_t ldq = 0;
+  FastDiv d;
+  __device__ __forceinline__ T at(uint32_t idx, int r) const {
+    if (A == nullptr) return T(1);
+    const uint32_t q = d.div(idx);
+    const uint32_t i = idx - q * d.d;
+    T v = A[i + int64_t(d.d) * r];
+    if (Q != nullptr) v *= Q[q + ldq * r];
+    return v;
+  }
+};
 
 // Geometry of one leading contraction (Algorithm 2 steps 4/7):
 // Y viewed as the J x K column-major matrix reshape(Y, [J_k, K_k]) (eq. 2.3).
-// Rows j index modes [0, k), columns c index modes [k, N).
+// Rows j index modes [0, k), columns c index modes [k, N).  J and K < 2^31.
 template <typename T>
 struct LeadArgs {
   const T* Y;
   int64_t J, K;
-  int N, k;                 // order and split (k leading modes in J)
   int R;                    // total rank
   int r0;                   // first rank column handled by this launch
-  int64_t I[kMaxOrder];
-  const T* A[kMaxOrder];    // factors, column-major I_m x R
+  KrRows<T> wl;             // W_L rows: Khatri-Rao over modes [0, k)
+  KrRows<T> wr;             // W_R rows: Khatri-Rao over modes [k, N)
   int64_t Kc;               // columns per K-split (multiple of the tile width)
   int nrt;                  // row tiles per J-block (1 whenever the R side runs)
   T* Rpart;                 // [nKs][R][J]  R-side partial sums (per K-split)
@@ -66,10 +101,13 @@ __device__ __forceinline__ T kr_entry(const T* const* A, const int64_t* I, int m
   T p = T(1);
   for (int m = m_begin; m < m_end; ++m) {
     const int64_t In = I[m];
-    const int64_t q = idx / In;
-    const int64_t i = idx - q * In;
-    p *= A[m][i + In * r];
-    idx = q;
+    if (m + 1 < m_end) {
+      const int64_t q = idx / In;
+      p *= A[m][(idx - q * In) + In * r];
+      idx = q;
+    } else {
+      p *= A[m][idx + In * r];
+    }
   }
   return p;
 }

@@ -17,6 +17,11 @@ SimtShape simt_shape_f64(int r);
 constexpr int kMaxRankTileF32 = 64;
 constexpr int kMaxRankTileF64 = 16;
 
+// Resident CTAs per SM of an instance (occupancy query; its design value
+// when no device is present).
+int lead_blocks_per_sm_f32(int RT, int sides);
+int lead_blocks_per_sm_f64(int RT, int sides);
+
 // sides: 1 = R side, 2 = L side, 3 = both.  grid = (nJb, nKs).
 cudaError_t launch_lead_f32(const LeadArgs<float>& a, int RT, int sides, dim3 grid, cudaStream_t st);
 cudaError_t launch_lead_f64(const LeadArgs<double>& a, int RT, int sides, dim3 grid, cudaStream_t st);

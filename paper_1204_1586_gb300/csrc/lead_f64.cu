@@ -7,7 +7,7 @@ namespace cpg {
 namespace {
 template <int RT, int TJ, int SIDES>
 cudaError_t run(const LeadArgs<double>& a, dim3 grid, cudaStream_t st) {
-  using C = SimtCfg<double, RT, TJ>;
+  using C = SimtCfg<double, RT, TJ, SIDES>;
   auto kern = lead_simt_kernel<double, RT, TJ, SIDES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
   if (e != cudaSuccess) return e;
@@ -25,9 +25,30 @@ cudaError_t run_sides(const LeadArgs<double>& a, int sides, dim3 grid, cudaStrea
   }
 }
 
+template <int RT, int TJ, int SIDES>
+int bps() {
+  using C = SimtCfg<double, RT, TJ, SIDES>;
+  int n = 0;
+  auto kern = lead_simt_kernel<double, RT, TJ, SIDES>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT, C::smem_bytes) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return C::MIN_BLOCKS;
+  }
+  return n;
+}
+
+template <int RT, int TJ>
+int bps_sides(int sides) {
+  static int cache[4] = {0, 0, 0, 0};
+  if (sides < 1 || sides > 3) return 1;
+  if (cache[sides] == 0) cache[sides] = sides == 1 ? bps<RT, TJ, 1>() : sides == 2 ? bps<RT, TJ, 2>() : bps<RT, TJ, 3>();
+  return cache[sides];
+}
+
 template <int RT, int TJ>
 SimtShape shape() {
-  using C = SimtCfg<double, RT, TJ>;
+  using C = SimtCfg<double, RT, TJ, 3>;
   return SimtShape{RT, TJ, C::TK, C::smem_bytes};
 }
 }  // namespace
@@ -36,6 +57,15 @@ SimtShape simt_shape_f64(int r) {
   if (r <= 4) return shape<4, 128>();
   if (r <= 8) return shape<8, 128>();
   return shape<16, 64>();
+}
+
+int lead_blocks_per_sm_f64(int RT, int sides) {
+  switch (RT) {
+    case 4: return bps_sides<4, 128>(sides);
+    case 8: return bps_sides<8, 128>(sides);
+    case 16: return bps_sides<16, 64>(sides);
+    default: return 1;
+  }
 }
 
 cudaError_t launch_lead_f64(const LeadArgs<double>& a, int RT, int sides, dim3 grid, cudaStream_t st) {

@@ -10,22 +10,23 @@
 //       W_L = A^(k) (.) ... (.) A^(1)     (Khatri-Rao over the leading modes)
 //
 // so that the all-mode gradient streams Y from memory once.  The Khatri-Rao
-// rows are generated per tile from the factor rows (the Kronecker build of
-// eq. 3.3 evaluated entry by entry) and never materialised in global memory.
+// rows are generated per tile in shared memory (one factor row times one
+// entry of a small Kronecker table, eq. 3.3) and never materialised in
+// global memory.
 //
 // Work split: CTA (jb, ks) owns the J-block of nrt row tiles
 // [jb*nrt*TJ, (jb+1)*nrt*TJ) and the column range [ks*Kc, ks*Kc+Kc); stage s
-// covers column chunk s / nrt and row tile s % nrt.  The R side needs its
-// accumulators for every row of the block, so it runs with nrt = 1; the
-// L side alone may use tall blocks (nrt > 1) to cut the number of J-block
-// partials.  It streams column chunks of TK through a multi-stage
-// cp.async pipeline into an XOR-swizzled shared tile that serves both access
-// patterns without bank conflicts:
+// covers column chunk s / nrt and row tile s % nrt.  The R side keeps its
+// accumulators for every row of the block in registers, so it runs with
+// nrt = 1; the L side alone may use tall blocks (nrt > 1) to cut the number
+// of J-block partials.  Chunks stream through a multi-stage cp.async pipeline
+// into an XOR-swizzled shared tile that serves both access patterns without
+// bank conflicts:
 //   R side: warp w takes columns w, w+8, ...; each lane holds RPL rows and
 //           accumulates all RT ranks over the CTA's columns in registers.
 //   L side: warp (wr, wc) takes a band of rows and TCL columns per lane and
 //           accumulates over rows; the WR row bands are summed through shared
-//           memory once per chunk.
+//           memory once per finished column chunk.
 // Outputs are deterministic partial sums: Rpart[ks] (over K-splits) and
 // Lpart[jb] (over J-blocks), summed in a fixed order by the chain kernels.
 #pragma once
@@ -34,8 +35,10 @@
 
 namespace cpg {
 
-template <typename T, int RT, int TJ>
+template <typename T, int RT, int TJ, int SIDES>
 struct SimtCfg {
+  static constexpr bool DO_R = (SIDES & 1) != 0;
+  static constexpr bool DO_L = (SIDES & 2) != 0;
   static constexpr int NT = 256;
   static constexpr int VEC = 16 / int(sizeof(T));        // elements per 16-byte chunk
   static constexpr int STAGE_BYTES = (TJ == 32) ? 16384 : 32768;
@@ -54,13 +57,19 @@ struct SimtCfg {
   static_assert(WC >= 1 && 8 % WC == 0, "bad L-side warp grid");
   static_assert(ROWS_PW % VEC == 0, "row band must hold whole chunks");
   static_assert(8 * RT <= STAGES * TK, "R-side reduction must fit in the tile buffers");
+  static_assert(NT % CPC == 0, "copy mapping needs whole columns per pass");
 
+  // The L-side row-band reduction reuses the stage buffer it has just consumed
+  // when it fits there.
+  static constexpr bool RED_ALIAS = size_t(WR) * RT * TK <= size_t(TK) * TJ;
   static constexpr size_t y_elems = size_t(STAGES) * TK * TJ;
-  static constexpr size_t wr_elems = size_t(2) * TK * RT;
-  static constexpr size_t wl_elems = size_t(2) * TJ * RT;
-  static constexpr size_t red_elems = (WR > 1) ? size_t(WR) * RT * TK : 0;
+  static constexpr size_t wr_elems = DO_R ? size_t(2) * TK * RT : 0;
+  static constexpr size_t wl_elems = DO_L ? size_t(DO_R ? 1 : 2) * TJ * RT : 0;
+  static constexpr size_t red_elems = (DO_L && WR > 1 && !RED_ALIAS) ? size_t(WR) * RT * TK : 0;
   static constexpr size_t smem_bytes = (y_elems + wr_elems + wl_elems + red_elems) * sizeof(T);
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
+  // Two CTAs per SM when both shared memory and a 128-register budget allow.
+  static constexpr int MIN_BLOCKS = (SIDES != 3 && RT <= 16 && 2 * (smem_bytes + 1024) <= 228 * 1024) ? 2 : 1;
 };
 
 // Swizzled position of element (c, j) inside one stage of the tile.
@@ -105,17 +114,17 @@ __device__ __forceinline__ void sts_vec(T* p, const T (&in)[N]) {
 
 // SIDES: bit 0 = R side (step 4), bit 1 = L side (step 7).
 template <typename T, int RT, int TJ, int SIDES>
-__global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) {
-  using C = SimtCfg<T, RT, TJ>;
-  constexpr bool DO_R = (SIDES & 1) != 0;
-  constexpr bool DO_L = (SIDES & 2) != 0;
+__global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
+    lead_simt_kernel(const LeadArgs<T> a) {
+  using C = SimtCfg<T, RT, TJ, SIDES>;
+  constexpr bool DO_R = C::DO_R, DO_L = C::DO_L;
   constexpr int NT = C::NT, VEC = C::VEC, TK = C::TK, STAGES = C::STAGES;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ys = reinterpret_cast<T*>(smem_raw);
   T* WRs = Ys + C::y_elems;
   T* WLs = WRs + C::wr_elems;
-  T* red = WLs + C::wl_elems;
+  T* red_sep = WLs + C::wl_elems;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t J = a.J, K = a.K;
@@ -130,18 +139,29 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
   const bool do_norm = DO_R && (a.normpart != nullptr);
 
   // Skipped (out-of-range) tile entries must read as finite values: zero once.
-  for (size_t f = tid; f < C::y_elems; f += NT) Ys[f] = T(0);
+  for (int f = tid; f < int(C::y_elems); f += NT) Ys[f] = T(0);
 
+  // Copy mapping: thread tid always moves chunk q = tid % CPC of columns
+  // tid / CPC + u * (NT / CPC), so its addresses advance by fixed strides.
+  constexpr int CSTEP = NT / C::CPC;                // columns per copy pass
+  const int cq = tid % C::CPC, cc0 = tid / C::CPC;
   auto issue = [&](int it) {
     if (it < nst) {
       T* dst = Ys + size_t(it % STAGES) * TK * TJ;
       const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
       const int64_t j0 = jblk + int64_t(it % nrt) * TJ;
       if (a.vec_ok) {
-        for (int f = tid; f < TK * C::CPC; f += NT) {
-          const int c = f / C::CPC, q = f % C::CPC;
-          const int64_t cg = cbase + c, jg = j0 + int64_t(q) * VEC;
-          if (cg < kend && jg < J) cp_async16(dst + c * TJ + ((q ^ (c & 7)) * VEC), a.Y + jg + J * cg);
+        const int64_t jg = j0 + int64_t(cq) * VEC;
+        if (jg < J) {
+          const T* src = a.Y + jg + J * (cbase + cc0);
+          const int64_t cstride = J * CSTEP;
+          const int64_t nc = kend - cbase;          // valid columns in this chunk
+#pragma unroll
+          for (int u = 0; u < TK / CSTEP; ++u) {
+            const int c = cc0 + u * CSTEP;
+            if (c < nc) cp_async16(dst + c * TJ + ((cq ^ (c & 7)) * VEC), src);
+            src += cstride;
+          }
         }
       } else {
         for (int f = tid; f < TK * TJ; f += NT) {
@@ -159,7 +179,7 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
     for (int f = tid; f < TJ * RT; f += NT) {
       const int j = f / RT, r = f % RT;
       const int64_t jg = j0 + j;
-      dst[f] = (jg < J && r0 + r < R) ? kr_entry<T>(a.A, a.I, 0, a.k, jg, r0 + r) : T(0);
+      dst[f] = (jg < J && r0 + r < R) ? a.wl.at(uint32_t(jg), r0 + r) : T(0);
     }
   };
   if constexpr (DO_L) {
@@ -167,8 +187,8 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
   }
   __syncthreads();
 
-  T racc[C::NLD][C::VECR][RT];
-  T lacc[C::TCL][RT];
+  T racc[C::NLD][C::VECR][DO_R ? RT : 1];
+  T lacc[C::TCL][DO_L ? RT : 1];
   double ss = 0.0;
   if constexpr (DO_R) {
 #pragma unroll
@@ -202,16 +222,16 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
       for (int f = tid; f < TK * RT; f += NT) {
         const int c = f / RT, r = f % RT;
         const int64_t cg = cbase + c;
-        Wr[f] = (cg < kend && r0 + r < R) ? kr_entry<T>(a.A, a.I, a.k, a.N, cg, r0 + r) : T(0);
+        Wr[f] = (cg < kend && r0 + r < R) ? a.wr.at(uint32_t(cg), r0 + r) : T(0);
       }
     }
-    if constexpr (DO_L) {
+    if constexpr (DO_L && !DO_R) {
       if (nrt > 1) gen_wl(WLs + size_t(it & 1) * TJ * RT, rt);
     }
     __syncthreads();
     issue(it + STAGES - 1);
 
-    const T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
+    T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
     if constexpr (DO_R) {
       const T* Wr = WRs + size_t(it & 1) * TK * RT;
 #pragma unroll 2
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
     }
 
     if constexpr (DO_L) {
-      const T* Wl = WLs + ((nrt > 1) ? size_t(it & 1) * TJ * RT : 0);
+      const T* Wl = WLs + ((!DO_R && nrt > 1) ? size_t(it & 1) * TJ * RT : 0);
 #pragma unroll 2
       for (int q = 0; q < C::ROWS_PW / VEC; ++q) {
         const int jl = wr * C::ROWS_PW + q * VEC;
@@ -273,6 +293,8 @@ __global__ void __launch_bounds__(256, 1) lead_simt_kernel(const LeadArgs<T> a) 
       if (rt == nrt - 1) {
         // The chunk's columns are complete over this J-block: sum the row bands.
         if constexpr (C::WR > 1) {
+          T* red = C::RED_ALIAS ? Yst : red_sep;
+          if constexpr (C::RED_ALIAS) __syncthreads();  // every warp is done reading this stage
 #pragma unroll
           for (int t = 0; t < C::TCL; ++t)
 #pragma unroll
