@@ -588,6 +588,13 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
   const size_t upd_smem = size_t(3) * R * R * sizeof(double);
   cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
+  int64_t imax = 1;
+  for (int m = 0; m < s.N; ++m) imax = std::max(imax, s.I[m]);
+  constexpr size_t kSmemCap = 200 * 1024;
+  const bool smem_path = als_smem_bytes(imax, R) <= kSmemCap;
+  if (smem_path)
+    cudaFuncSetAttribute(als_update_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(als_smem_bytes(imax, R)));
 
   auto update = [&](int n, double* fit_out) {
     AlsArgs<T> u{};
@@ -604,7 +611,10 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     u.fit_out = fit_out;
     u.normY2 = w.h.normY2;
     ++g_launches;
-    als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
+    if (smem_path)
+      als_update_smem_kernel<T><<<1, 512, als_smem_bytes(s.I[n], R), st>>>(u);
+    else
+      als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
   };
 
   for (int it = 0; it < iters; ++it) {

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
 
   T racc[C::NLD][C::VECR][DO_R ? RT : 1];
   T lacc[C::TCL][DO_L ? RT : 1];
-  double ss = 0.0;
+  T ss = T(0);  // this thread's sum of y^2 (fixed order); summed in FP64 across threads
   if constexpr (DO_R) {
 #pragma unroll
     for (int m = 0; m < C::NLD; ++m)
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
 #pragma unroll
             for (int m = 0; m < C::NLD; ++m)
 #pragma unroll
-              for (int e = 0; e < C::VECR; ++e) ss += double(y[m][e]) * double(y[m][e]);
+              for (int e = 0; e < C::VECR; ++e) ss = fma(y[m][e], y[m][e], ss);
           }
         }
       }
@@ -352,11 +352,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       if (r0 + r < R && jg < J) a.Rpart[(int64_t(ks) * R + r0 + r) * J + jg] = sum;
     }
     if (do_norm) {
+      double sd = double(ss);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
       __syncthreads();
       double* wsum = reinterpret_cast<double*>(smem_raw);
-      if (lane == 0) wsum[warp] = ss;
+      if (lane == 0) wsum[warp] = sd;
       __syncthreads();
       if (tid == 0) {
         double t = 0.0;

@@ -193,7 +193,11 @@ def test_als_noiseless_fit_to_one(cg):
     Ad = [dev_factor(a, np.float64) for a in A0]
     lam, fit = cg.cp_als_iter(torch.from_numpy(y).cuda(), I, Ad, 100, precision="fp64")
     torch.cuda.synchronize()
-    assert fit.cpu().numpy()[-1] > 1 - 1e-8
+    # The cheap fit cancels O(||Y||^2) terms, so in FP64 it resolves a misfit
+    # only down to about sqrt(eps) ~ 1.5e-8; the explicit fit has no such floor.
+    assert fit.cpu().numpy()[-1] > 1 - 1e-7
+    A = [a.cpu().numpy() for a in Ad]
+    assert oracle.cp_fit_direct(y, A, lam.cpu().numpy()) > 1 - 1e-10
 
 
 def test_als_singular_status(cg):

@@ -163,7 +163,9 @@ def test_als_noiseless_fit_to_one_and_monotone():
         A0 = cpsynth.gaussian_factors(I, R, seed=seed)
         tr = oracle.cp_als(y, I, A0, iters=150, direct_fit=True)
         if converges:
-            assert tr.fits[-1] > 1 - 1e-8
+            # the cheap fit bottoms out near sqrt(eps) (cancellation); the explicit one does not
+            assert tr.fits[-1] > 1 - 1e-7
+            assert tr.fits_direct[-1] > 1 - 1e-10
         d = np.array(tr.fits_direct)
         assert np.all(np.diff(d) >= -1e-12)
         np.testing.assert_allclose(tr.fits, tr.fits_direct, atol=1e-9)
