@@ -1,0 +1,246 @@
+// CP_ALS factor update (eq. 2.14, fast ALS of Section 4) for FP32 tensors,
+// with the normal equations carried in double-float arithmetic (dfloat.cuh).
+//
+// For mode n, with the gradient G = Y_(n) KR from the chain kernels:
+//   V        = Hadamard_{m != n} Gram_m          (Gram_m = A^(m)T A^(m))
+//   V        = L L^T                             (Cholesky)
+//   X        = G V^{-1}                          (forward + back substitution per row)
+//   lambda_q = ||x_q||,  a_q = x_q / lambda_q    (column normalisation)
+//   Gram_n   = A^(n)T A^(n) of the stored FP32 factor (products exact, sums compensated)
+// and after the last mode of a sweep the fit from R x R quantities:
+//   <Y, Yhat> = sum_q lambda_q a_q^T g_q,  ||Yhat||^2 = lambda^T (Hadamard_m Gram_m) lambda,
+//   fit = 1 - sqrt(max(0, ||Y||^2 - 2 <Y,Yhat> + ||Yhat||^2)) / ||Y||.
+// Every quantity of the normal equations is a double-float (about 48-bit
+// significand) so that their conditioning is handled at FP64-like accuracy on
+// the FP32 pipe; the measured FP64 rate of this GPU (64-cycle dependent FMA,
+// ~680-cycle divide) would put tens of microseconds on the critical path of
+// every update.  A V whose pivot is not positive leaves A^(n), lambda and
+// Gram_n untouched and records CPG_ERR_SINGULAR in the device status word.
+#pragma once
+
+#include "chain.cuh"
+#include "common.cuh"
+#include "dfloat.cuh"
+
+namespace cpg {
+
+struct AlsDfArgs {
+  int N, n, R;
+  int64_t In;
+  df* grams;              // [N][R][R] double-float Grams
+  const float* G;         // In x R, column-major
+  float* An;              // In x R, column-major (updated in place)
+  double* lambda;         // [R]
+  int* status;            // device status word
+  double* fit_out;        // fit of this sweep, or nullptr
+  const double* normY2;   // ||Y||^2
+};
+
+// Gram matrices of all N factors.  grid = (ceil(R*R/256), N).
+__global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
+  const int m = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= R * R) return;
+  const int a = t % R, b = t / R;
+  const int64_t In = f.I[m];
+  const float* A = f.A[m];
+  df s{0.f, 0.f};
+  for (int64_t i = 0; i < In; ++i) s = df_add_prod_ff(s, A[i + In * a], A[i + In * b]);
+  grams[(int64_t(m) * R + b) * R + a] = s;
+}
+
+inline size_t als_df_smem_bytes(int64_t In, int R) {
+  const size_t RS = size_t(R) + 1;
+  return size_t(R) * R * sizeof(df) + 3 * size_t(R) * sizeof(df) + size_t(In) * RS * (sizeof(df) + sizeof(float)) + 16;
+}
+
+__device__ __forceinline__ df df_warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
+}
+
+// One block (512 threads).  Shared memory: als_df_smem_bytes(In, R).
+__global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int R = a.R, N = a.N, n = a.n, RS = R + 1;
+  const int64_t In = a.In;
+  df* V = reinterpret_cast<df*>(smraw);      // V, then L (lower, V[i + R*j])
+  df* dinv = V + R * R;                      // 1 / L[j][j]
+  df* lam = dinv + R;                        // lambda_q
+  df* ilam = lam + R;                        // 1 / lambda_q
+  df* X = ilam + R;                          // X[i*RS + q]
+  float* Af = reinterpret_cast<float*>(X + In * RS);  // stored factor, Af[i*RS + q]
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+
+  for (int64_t t = tid; t < In * R; t += nt) {
+    const int q = int(t / In);
+    const int64_t i = t - int64_t(q) * In;
+    X[i * RS + q] = df_make(a.G[t]);
+  }
+  for (int t = tid; t < R * R; t += nt) {
+    df v{1.f, 0.f};
+    for (int m = 0; m < N; ++m)
+      if (m != n) v = df_mul(v, a.grams[int64_t(m) * R * R + t]);
+    V[t] = v;
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+
+  // Right-looking Cholesky: V = L L^T.
+  if (R <= 32) {
+    if (warp == 0) {
+      for (int j = 0; j < R; ++j) {
+        const df d = V[j + R * j];
+        if (!(d.hi > 0.f)) {
+          if (lane == 0) fail = 1;
+          break;
+        }
+        const df piv = df_sqrt(d);
+        const df inv = df_div(df_make(1.f), piv);
+        __syncwarp();
+        if (lane == j) {
+          V[j + R * j] = piv;
+          dinv[j] = inv;
+        }
+        if (lane > j && lane < R) V[lane + R * j] = df_mul(V[lane + R * j], inv);
+        __syncwarp();
+        const int m = R - 1 - j;
+        for (int e = lane; e < m * m; e += 32) {
+          const int ii = j + 1 + e % m, ll = j + 1 + e / m;
+          if (ll <= ii) V[ii + R * ll] = df_sub(V[ii + R * ll], df_mul(V[ii + R * j], V[ll + R * j]));
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  } else {
+    for (int j = 0; j < R; ++j) {
+      const df d = V[j + R * j];
+      if (!(d.hi > 0.f)) {
+        if (tid == 0) fail = 1;
+        break;  // every thread reads the same d
+      }
+      const df piv = df_sqrt(d);
+      const df inv = df_div(df_make(1.f), piv);
+      __syncthreads();
+      if (tid == j) {
+        V[j + R * j] = piv;
+        dinv[j] = inv;
+      }
+      for (int i = j + 1 + tid; i < R; i += nt) V[i + R * j] = df_mul(V[i + R * j], inv);
+      __syncthreads();
+      const int m = R - 1 - j;
+      for (int e = tid; e < m * m; e += nt) {
+        const int ii = j + 1 + e % m, ll = j + 1 + e / m;
+        if (ll <= ii) V[ii + R * ll] = df_sub(V[ii + R * ll], df_mul(V[ii + R * j], V[ll + R * j]));
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) atomicCAS(a.status, 0, int(CPG_ERR_SINGULAR));
+    return;
+  }
+
+  // X = G V^{-1}: row i solves L z = g_i, then L^T x = z (in place).  Two
+  // interleaved partial sums shorten the dependent chain.
+  for (int64_t i = tid; i < In; i += nt) {
+    df* x = X + i * RS;
+    for (int j = 0; j < R; ++j) {
+      df s0 = x[j], s1{0.f, 0.f};
+      int p = 0;
+      for (; p + 1 < j; p += 2) {
+        s0 = df_sub(s0, df_mul(V[j + R * p], x[p]));
+        s1 = df_sub(s1, df_mul(V[j + R * (p + 1)], x[p + 1]));
+      }
+      if (p < j) s0 = df_sub(s0, df_mul(V[j + R * p], x[p]));
+      x[j] = df_mul(df_add(s0, s1), dinv[j]);
+    }
+    for (int j = R - 1; j >= 0; --j) {
+      df s0 = x[j], s1{0.f, 0.f};
+      int p = j + 1;
+      for (; p + 1 < R; p += 2) {
+        s0 = df_sub(s0, df_mul(V[p + R * j], x[p]));
+        s1 = df_sub(s1, df_mul(V[(p + 1) + R * j], x[p + 1]));
+      }
+      if (p < R) s0 = df_sub(s0, df_mul(V[p + R * j], x[p]));
+      x[j] = df_mul(df_add(s0, s1), dinv[j]);
+    }
+  }
+  __syncthreads();
+
+  // lambda_q = ||x_q||.
+  for (int q = warp; q < R; q += nw) {
+    df s{0.f, 0.f};
+    for (int64_t i = lane; i < In; i += 32) s = df_add(s, df_mul(X[i * RS + q], X[i * RS + q]));
+    s = df_warp_sum(s);
+    if (lane == 0) {
+      const df l = df_sqrt(s);
+      lam[q] = l;
+      ilam[q] = (l.hi > 0.f) ? df_div(df_make(1.f), l) : df_make(1.f);
+      a.lambda[q] = df_to_double(l);
+    }
+  }
+  __syncthreads();
+  for (int64_t t = tid; t < In * R; t += nt) {
+    const int q = int(t / In);
+    const int64_t i = t - int64_t(q) * In;
+    const df v = df_mul(X[i * RS + q], ilam[q]);
+    const float f = __fadd_rn(v.hi, v.lo);
+    a.An[t] = f;
+    Af[i * RS + q] = f;
+  }
+  __syncthreads();
+
+  // Gram of the stored factor, one warp per (p <= q) pair.
+  df* gn = a.grams + int64_t(n) * R * R;
+  const int npairs = R * (R + 1) / 2;
+  for (int pq = warp; pq < npairs; pq += nw) {
+    int p = 0, rem = pq;
+    while (rem >= R - p) {
+      rem -= R - p;
+      ++p;
+    }
+    const int q = p + rem;
+    df s{0.f, 0.f};
+    for (int64_t i = lane; i < In; i += 32) s = df_add_prod_ff(s, Af[i * RS + p], Af[i * RS + q]);
+    s = df_warp_sum(s);
+    if (lane == 0) {
+      gn[p + R * q] = s;
+      gn[q + R * p] = s;
+    }
+  }
+  if (a.fit_out == nullptr) return;
+  __syncthreads();
+  df* part = V;  // free now
+  for (int q = warp; q < R; q += nw) {
+    df s{0.f, 0.f};
+    for (int64_t i = lane; i < In; i += 32) s = df_add_prod_ff(s, Af[i * RS + q], a.G[i + In * q]);
+    s = df_warp_sum(s);
+    if (lane == 0) part[q] = df_mul(lam[q], s);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    df inner{0.f, 0.f}, model{0.f, 0.f};
+    for (int q = lane; q < R; q += 32) inner = df_add(inner, part[q]);
+    for (int t = lane; t < R * R; t += 32) {
+      df v = df_mul(lam[t % R], lam[t / R]);
+      for (int m = 0; m < N; ++m) v = df_mul(v, a.grams[int64_t(m) * R * R + t]);
+      model = df_add(model, v);
+    }
+    inner = df_warp_sum(inner);
+    model = df_warp_sum(model);
+    if (lane == 0) {
+      const df y2 = df_from_double(*a.normY2);
+      df res = df_add(df_sub(y2, df_add(inner, inner)), model);
+      if (!(res.hi > 0.f)) res = df{0.f, 0.f};
+      const df ratio = df_div(df_sqrt(res), df_sqrt(y2));
+      *a.fit_out = 1.0 - df_to_double(ratio);
+    }
+  }
+}
+
+}  // namespace cpg

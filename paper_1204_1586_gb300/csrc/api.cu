@@ -4,8 +4,10 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include "als.cuh"
+#include "als_df.cuh"
 #include "chain.cuh"
 #include "common.cuh"
 #include "lead_dispatch.cuh"
@@ -584,37 +586,64 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
   const void* const* Ac = const_cast<const void* const*>(A);
 
+  constexpr bool kDf = std::is_same_v<T, float>;
   ++g_launches;
-  gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
+  if constexpr (kDf)
+    gram_all_df_kernel<<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R,
+                                                                                    reinterpret_cast<df*>(w.grams));
+  else
+    gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
   const size_t upd_smem = size_t(3) * R * R * sizeof(double);
-  cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
   int64_t imax = 1;
   for (int m = 0; m < s.N; ++m) imax = std::max(imax, s.I[m]);
   constexpr size_t kSmemCap = 200 * 1024;
-  const bool smem_path = als_smem_bytes(imax, R) <= kSmemCap;
-  if (smem_path)
-    cudaFuncSetAttribute(als_update_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(als_smem_bytes(imax, R)));
+  const bool smem_path = (kDf ? als_df_smem_bytes(imax, R) : als_smem_bytes(imax, R)) <= kSmemCap;
+  if constexpr (kDf) {
+    if (!smem_path) return CPG_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(als_update_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(als_df_smem_bytes(imax, R)));
+  } else {
+    cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
+    if (smem_path)
+      cudaFuncSetAttribute(als_update_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(als_smem_bytes(imax, R)));
+  }
 
   auto update = [&](int n, double* fit_out) {
-    AlsArgs<T> u{};
-    u.N = s.N;
-    u.n = n;
-    u.R = R;
-    u.In = s.I[n];
-    u.grams = w.grams;
-    u.G = w.G;
-    u.An = static_cast<T*>(A[n]);
-    u.lambda = lambda;
-    u.X = w.X;
-    u.status = w.h.status;
-    u.fit_out = fit_out;
-    u.normY2 = w.h.normY2;
     ++g_launches;
-    if (smem_path)
-      als_update_smem_kernel<T><<<1, 512, als_smem_bytes(s.I[n], R), st>>>(u);
-    else
-      als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
+    if constexpr (kDf) {
+      AlsDfArgs u{};
+      u.N = s.N;
+      u.n = n;
+      u.R = R;
+      u.In = s.I[n];
+      u.grams = reinterpret_cast<df*>(w.grams);
+      u.G = w.G;
+      u.An = static_cast<float*>(A[n]);
+      u.lambda = lambda;
+      u.status = w.h.status;
+      u.fit_out = fit_out;
+      u.normY2 = w.h.normY2;
+      als_update_df_kernel<<<1, 512, als_df_smem_bytes(s.I[n], R), st>>>(u);
+    } else {
+      AlsArgs<T> u{};
+      u.N = s.N;
+      u.n = n;
+      u.R = R;
+      u.In = s.I[n];
+      u.grams = w.grams;
+      u.G = w.G;
+      u.An = static_cast<T*>(A[n]);
+      u.lambda = lambda;
+      u.X = w.X;
+      u.status = w.h.status;
+      u.fit_out = fit_out;
+      u.normY2 = w.h.normY2;
+      if (smem_path)
+        als_update_smem_kernel<T><<<1, 512, als_smem_bytes(s.I[n], R), st>>>(u);
+      else
+        als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
+    }
   };
 
   for (int it = 0; it < iters; ++it) {

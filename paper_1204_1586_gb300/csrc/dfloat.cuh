@@ -1,0 +1,94 @@
+// Double-float ("double-single") arithmetic on the FP32 pipe: a value is the
+// unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, giving a
+// significand of about 48 bits.  Built from error-free transformations:
+//   TwoSum (Knuth, TAOCP vol. 2): s + e == a + b exactly;
+//   TwoProd via FMA (Dekker 1971 with a fused multiply-add): p + e == a * b exactly;
+// with the add/multiply/divide/sqrt compositions of the double-double
+// literature (Hida, Li, Bailey, "Algorithms for quad-double precision
+// floating point arithmetic", 2001), written here for float pairs.
+// The _rn intrinsics keep the compiler from fusing the compensation terms.
+#pragma once
+
+namespace cpg {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float a) { return df{a, 0.0f}; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return df{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+
+// a * b for a float b (one fewer cross term).
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+
+// acc + a * b with a, b floats: the product is exact before the addition.
+__device__ __forceinline__ df df_add_prod_ff(df acc, float a, float b) { return df_add(acc, two_prod(a, b)); }
+
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_sub(a, df_mul_f(b, q1));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  r = df_sub(r, df_mul_f(b, q2));
+  const float q3 = __fdiv_rn(r.hi, b.hi);
+  df q = quick_two_sum(q1, q2);
+  return df_add(q, df_make(q3));
+}
+
+__device__ __forceinline__ df df_sqrt(df a) {
+  if (a.hi <= 0.0f) return df{0.0f, 0.0f};
+  const float s = __fsqrt_rn(a.hi);
+  const df r = df_sub(a, two_prod(s, s));        // a - s^2
+  return quick_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }
+
+__device__ __forceinline__ df df_from_double(double d) {
+  const float hi = float(d);
+  return df{hi, float(d - double(hi))};
+}
+
+__device__ __forceinline__ df df_shfl_xor(df a, int o) {
+  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+}  // namespace cpg
