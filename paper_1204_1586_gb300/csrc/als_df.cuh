@@ -4,7 +4,7 @@
 // For mode n, with the gradient G = Y_(n) KR from the chain kernels:
 //   V        = Hadamard_{m != n} Gram_m          (Gram_m = A^(m)T A^(m))
 //   V        = L L^T                             (Cholesky)
-//   X        = G V^{-1}                          (forward + back substitution per row)
+//   X        = G V^{-1}                          (V^{-1} = L^{-T} L^{-1})
 //   lambda_q = ||x_q||,  a_q = x_q / lambda_q    (column normalisation)
 //   Gram_n   = A^(n)T A^(n) of the stored FP32 factor (products exact, sums compensated)
 // and after the last mode of a sweep the fit from R x R quantities:
@@ -51,7 +51,8 @@ __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
 
 inline size_t als_df_smem_bytes(int64_t In, int R) {
   const size_t RS = size_t(R) + 1;
-  return size_t(R) * R * sizeof(df) + 3 * size_t(R) * sizeof(df) + size_t(In) * RS * (sizeof(df) + sizeof(float)) + 16;
+  return 3 * size_t(R) * R * sizeof(df) + 4 * size_t(R) * sizeof(df) + size_t(In) * RS * (sizeof(df) + sizeof(float)) +
+         16;
 }
 
 __device__ __forceinline__ df df_warp_sum(df v) {
@@ -60,35 +61,48 @@ __device__ __forceinline__ df df_warp_sum(df v) {
   return v;
 }
 
-// One block (512 threads).  Shared memory: als_df_smem_bytes(In, R).
-__global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
+constexpr int kAlsThreads = 1024;
+
+// One block of kAlsThreads threads.  Shared memory: als_df_smem_bytes(In, R).
+// Phases (each a short dependent chain, all rows / columns in parallel):
+//   Cholesky    right-looking, pivots from a reciprocal square root (no divide)
+//   L^{-1}      column c by R rank-1 steps (lane c owns its column)
+//   V^{-1}      = L^{-T} L^{-1}, one output per thread
+//   X           = G V^{-1}, one output per thread
+//   lambda      warp per column; Gram: 8 lanes per (p, q) pair.
+__global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int R = a.R, N = a.N, n = a.n, RS = R + 1;
   const int64_t In = a.In;
   df* V = reinterpret_cast<df*>(smraw);      // V, then L (lower, V[i + R*j])
-  df* dinv = V + R * R;                      // 1 / L[j][j]
+  df* Li = V + R * R;                        // L^{-1} (lower, Li[i + R*c])
+  df* Vi = Li + R * R;                       // V^{-1}
+  df* dinv = Vi + R * R;                     // 1 / L[j][j]
   df* lam = dinv + R;                        // lambda_q
   df* ilam = lam + R;                        // 1 / lambda_q
-  df* X = ilam + R;                          // X[i*RS + q]
-  float* Af = reinterpret_cast<float*>(X + In * RS);  // stored factor, Af[i*RS + q]
+  df* part = ilam + R;                       // per-column partial inner products
+  df* X = part + R;                          // X[i*RS + q]
+  float* Af = reinterpret_cast<float*>(X + In * RS);  // G, then the stored factor: Af[i*RS + q]
   __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
   for (int64_t t = tid; t < In * R; t += nt) {
     const int q = int(t / In);
     const int64_t i = t - int64_t(q) * In;
-    X[i * RS + q] = df_make(a.G[t]);
+    Af[i * RS + q] = a.G[t];
   }
   for (int t = tid; t < R * R; t += nt) {
     df v{1.f, 0.f};
     for (int m = 0; m < N; ++m)
       if (m != n) v = df_mul(v, a.grams[int64_t(m) * R * R + t]);
     V[t] = v;
+    const int i = t % R, c = t / R;
+    Li[t] = df_make(i == c ? 1.f : 0.f);
   }
   if (tid == 0) fail = 0;
   __syncthreads();
 
-  // Right-looking Cholesky: V = L L^T.
+  // Right-looking Cholesky V = L L^T; sqrt(d) = d * rsqrt(d), 1/L[j][j] = rsqrt(d).
   if (R <= 32) {
     if (warp == 0) {
       for (int j = 0; j < R; ++j) {
@@ -97,14 +111,13 @@ __global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
           if (lane == 0) fail = 1;
           break;
         }
-        const df piv = df_sqrt(d);
-        const df inv = df_div(df_make(1.f), piv);
+        const df rs = df_rsqrt(d);
         __syncwarp();
         if (lane == j) {
-          V[j + R * j] = piv;
-          dinv[j] = inv;
+          V[j + R * j] = df_mul(d, rs);
+          dinv[j] = rs;
         }
-        if (lane > j && lane < R) V[lane + R * j] = df_mul(V[lane + R * j], inv);
+        if (lane > j && lane < R) V[lane + R * j] = df_mul(V[lane + R * j], rs);
         __syncwarp();
         const int m = R - 1 - j;
         for (int e = lane; e < m * m; e += 32) {
@@ -114,22 +127,20 @@ __global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
         __syncwarp();
       }
     }
-    __syncthreads();
   } else {
     for (int j = 0; j < R; ++j) {
       const df d = V[j + R * j];
       if (!(d.hi > 0.f)) {
         if (tid == 0) fail = 1;
-        break;  // every thread reads the same d
+        break;  // every thread read the same d
       }
-      const df piv = df_sqrt(d);
-      const df inv = df_div(df_make(1.f), piv);
+      const df rs = df_rsqrt(d);
       __syncthreads();
       if (tid == j) {
-        V[j + R * j] = piv;
-        dinv[j] = inv;
+        V[j + R * j] = df_mul(d, rs);
+        dinv[j] = rs;
       }
-      for (int i = j + 1 + tid; i < R; i += nt) V[i + R * j] = df_mul(V[i + R * j], inv);
+      for (int i = j + 1 + tid; i < R; i += nt) V[i + R * j] = df_mul(V[i + R * j], rs);
       __syncthreads();
       const int m = R - 1 - j;
       for (int e = tid; e < m * m; e += nt) {
@@ -138,50 +149,66 @@ __global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
       }
       __syncthreads();
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (fail) {
     if (tid == 0) atomicCAS(a.status, 0, int(CPG_ERR_SINGULAR));
     return;
   }
 
-  // X = G V^{-1}: row i solves L z = g_i, then L^T x = z (in place).  Two
-  // interleaved partial sums shorten the dependent chain.
-  for (int64_t i = tid; i < In; i += nt) {
-    df* x = X + i * RS;
-    for (int j = 0; j < R; ++j) {
-      df s0 = x[j], s1{0.f, 0.f};
-      int p = 0;
-      for (; p + 1 < j; p += 2) {
-        s0 = df_sub(s0, df_mul(V[j + R * p], x[p]));
-        s1 = df_sub(s1, df_mul(V[j + R * (p + 1)], x[p + 1]));
-      }
-      if (p < j) s0 = df_sub(s0, df_mul(V[j + R * p], x[p]));
-      x[j] = df_mul(df_add(s0, s1), dinv[j]);
-    }
-    for (int j = R - 1; j >= 0; --j) {
-      df s0 = x[j], s1{0.f, 0.f};
-      int p = j + 1;
-      for (; p + 1 < R; p += 2) {
-        s0 = df_sub(s0, df_mul(V[p + R * j], x[p]));
-        s1 = df_sub(s1, df_mul(V[(p + 1) + R * j], x[p + 1]));
-      }
-      if (p < R) s0 = df_sub(s0, df_mul(V[p + R * j], x[p]));
-      x[j] = df_mul(df_add(s0, s1), dinv[j]);
+  // L^{-1}: thread c owns column c; step j finalises row j and eliminates it below.
+  for (int c = tid; c < R; c += nt) {
+    for (int j = c; j < R; ++j) {
+      const df t = df_mul(Li[j + R * c], dinv[j]);
+      Li[j + R * c] = t;
+      for (int i = j + 1; i < R; ++i) Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], t));
     }
   }
   __syncthreads();
+  // V^{-1} = L^{-T} L^{-1}.
+  for (int t = tid; t < R * R; t += nt) {
+    const int p = t % R, q = t / R;
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
+    int i = p > q ? p : q;
+    for (; i + 1 < R; i += 2) {
+      s0 = df_add(s0, df_mul(Li[i + R * p], Li[i + R * q]));
+      s1 = df_add(s1, df_mul(Li[i + 1 + R * p], Li[i + 1 + R * q]));
+    }
+    if (i < R) s0 = df_add(s0, df_mul(Li[i + R * p], Li[i + R * q]));
+    Vi[t] = df_add(s0, s1);
+  }
+  __syncthreads();
+  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q].
+  for (int64_t t = tid; t < In * R; t += nt) {
+    const int q = int(t / In);
+    const int64_t i = t - int64_t(q) * In;
+    const float* g = Af + i * RS;
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
+    int p = 0;
+    for (; p + 1 < R; p += 2) {
+      s0 = df_add(s0, df_mul_f(Vi[p + R * q], g[p]));
+      s1 = df_add(s1, df_mul_f(Vi[p + 1 + R * q], g[p + 1]));
+    }
+    if (p < R) s0 = df_add(s0, df_mul_f(Vi[p + R * q], g[p]));
+    X[i * RS + q] = df_add(s0, s1);
+  }
+  __syncthreads();
 
-  // lambda_q = ||x_q||.
+  // lambda_q = ||x_q||, 1/lambda_q = rsqrt(||x_q||^2).
   for (int q = warp; q < R; q += nw) {
     df s{0.f, 0.f};
     for (int64_t i = lane; i < In; i += 32) s = df_add(s, df_mul(X[i * RS + q], X[i * RS + q]));
     s = df_warp_sum(s);
     if (lane == 0) {
-      const df l = df_sqrt(s);
-      lam[q] = l;
-      ilam[q] = (l.hi > 0.f) ? df_div(df_make(1.f), l) : df_make(1.f);
-      a.lambda[q] = df_to_double(l);
+      if (s.hi > 0.f) {
+        const df rs = df_rsqrt(s);
+        lam[q] = df_mul(s, rs);
+        ilam[q] = rs;
+      } else {
+        lam[q] = df{0.f, 0.f};
+        ilam[q] = df_make(1.f);
+      }
+      a.lambda[q] = df_to_double(lam[q]);
     }
   }
   __syncthreads();
@@ -195,27 +222,32 @@ __global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
   }
   __syncthreads();
 
-  // Gram of the stored factor, one warp per (p <= q) pair.
+  // Gram of the stored factor: 8 lanes per (p <= q) pair.
   df* gn = a.grams + int64_t(n) * R * R;
   const int npairs = R * (R + 1) / 2;
-  for (int pq = warp; pq < npairs; pq += nw) {
-    int p = 0, rem = pq;
-    while (rem >= R - p) {
-      rem -= R - p;
-      ++p;
-    }
-    const int q = p + rem;
+  const int sub = tid & 7, ngroups = nt >> 3;
+  for (int pq0 = 0; pq0 < npairs; pq0 += ngroups) {
+    const int pq = pq0 + (tid >> 3);
+    int p = 0, q = 0;
     df s{0.f, 0.f};
-    for (int64_t i = lane; i < In; i += 32) s = df_add_prod_ff(s, Af[i * RS + p], Af[i * RS + q]);
-    s = df_warp_sum(s);
-    if (lane == 0) {
+    if (pq < npairs) {
+      int rem = pq;
+      while (rem >= R - p) {
+        rem -= R - p;
+        ++p;
+      }
+      q = p + rem;
+      for (int64_t i = sub; i < In; i += 8) s = df_add_prod_ff(s, Af[i * RS + p], Af[i * RS + q]);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o, 8));
+    if (pq < npairs && sub == 0) {
       gn[p + R * q] = s;
       gn[q + R * p] = s;
     }
   }
   if (a.fit_out == nullptr) return;
   __syncthreads();
-  df* part = V;  // free now
   for (int q = warp; q < R; q += nw) {
     df s{0.f, 0.f};
     for (int64_t i = lane; i < In; i += 32) s = df_add_prod_ff(s, Af[i * RS + q], a.G[i + In * q]);
@@ -237,7 +269,7 @@ __global__ void __launch_bounds__(512) als_update_df_kernel(const AlsDfArgs a) {
       const df y2 = df_from_double(*a.normY2);
       df res = df_add(df_sub(y2, df_add(inner, inner)), model);
       if (!(res.hi > 0.f)) res = df{0.f, 0.f};
-      const df ratio = df_div(df_sqrt(res), df_sqrt(y2));
+      const df ratio = df_mul(df_sqrt(res), df_rsqrt(y2));
       *a.fit_out = 1.0 - df_to_double(ratio);
     }
   }

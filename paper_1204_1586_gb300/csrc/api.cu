@@ -624,7 +624,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.status = w.h.status;
       u.fit_out = fit_out;
       u.normY2 = w.h.normY2;
-      als_update_df_kernel<<<1, 512, als_df_smem_bytes(s.I[n], R), st>>>(u);
+      als_update_df_kernel<<<1, kAlsThreads, als_df_smem_bytes(s.I[n], R), st>>>(u);
     } else {
       AlsArgs<T> u{};
       u.N = s.N;

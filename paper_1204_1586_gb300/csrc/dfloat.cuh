@@ -80,6 +80,15 @@ __device__ __forceinline__ df df_sqrt(df a) {
   return quick_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
 }
 
+// 1 / sqrt(a) for a > 0: FP32 reciprocal-sqrt seed, then one Newton step
+// y <- y + y (1 - a y^2) / 2 carried in double-float (doubles the 24 seed bits).
+__device__ __forceinline__ df df_rsqrt(df a) {
+  const float y0 = rsqrtf(a.hi);
+  const df y = df_make(y0);
+  const df e = df_sub(df_make(1.f), df_mul(a, df_mul(y, y)));  // 1 - a y^2
+  return df_add(y, df_mul_f(df_mul(y, e), 0.5f));
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }
 
 __device__ __forceinline__ df df_from_double(double d) {
@@ -87,8 +96,8 @@ __device__ __forceinline__ df df_from_double(double d) {
   return df{hi, float(d - double(hi))};
 }
 
-__device__ __forceinline__ df df_shfl_xor(df a, int o) {
-  return df{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+__device__ __forceinline__ df df_shfl_xor(df a, int o, int width = 32) {
+  return df{__shfl_xor_sync(0xffffffffu, a.hi, o, width), __shfl_xor_sync(0xffffffffu, a.lo, o, width)};
 }
 
 }  // namespace cpg
