@@ -154,6 +154,34 @@ int cpg_profile_lead(int enable);
  * error. */
 int cpg_profile_read(float* ms, int* sides, int max);
 
+/* Size of the fixed device scratch array used by cp_gradient_all_noalloc
+ * (64 MiB, held by every GPU that loads the library until the process exits). */
+#define CPG_NOALLOC_WORKSPACE_BYTES (64u << 20)
+
+/* All-mode CP gradient without any device allocation, for callers that cannot
+ * call cudaMalloc: for example a plugin inside a host application that owns
+ * every device allocation through its own pool, or latency-critical code that
+ * must not allocate after start-up.  The paper has no counterpart; this is a
+ * calling convention of this library.
+ *
+ * Same computation and arguments as cp_gradient_all (Y, A, G are caller
+ * device buffers), but the scratch comes from a fixed array of
+ * CPG_NOALLOC_WORKSPACE_BYTES inside the library instead of opts->workspace.
+ * precision and split are as in cpg_opts; stream is a cudaStream_t (NULL =
+ * legacy default stream).
+ *  - Returns CPG_ERR_WORKSPACE when cpg_workspace_size(I, N, R, ...,
+ *    CPG_CALL_GRADIENT_ALL) exceeds CPG_NOALLOC_WORKSPACE_BYTES, and the
+ *    argument errors of cp_gradient_all otherwise; nothing is launched then.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array and leaves its contents behind.  Calls
+ *    that overlap on the GPU (different streams or threads) race on it;
+ *    calls on one stream are ordered.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+cpg_status cp_gradient_all_noalloc(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                                   void* const* G, int precision, int split, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
