@@ -56,6 +56,7 @@ SimtShape shape() {
 SimtShape simt_shape_f32(int r) {
   if (r <= 4) return shape<4, 256>();
   if (r <= 8) return shape<8, 256>();
+  if (r <= 10) return shape<10, 128>();
   if (r <= 12) return shape<12, 128>();
   if (r <= 16) return shape<16, 128>();
   if (r <= 24) return shape<24, 64>();
@@ -68,6 +69,7 @@ int lead_blocks_per_sm_f32(int RT, int sides) {
   switch (RT) {
     case 4: return bps_sides<4, 256>(sides);
     case 8: return bps_sides<8, 256>(sides);
+    case 10: return bps_sides<10, 128>(sides);
     case 12: return bps_sides<12, 128>(sides);
     case 16: return bps_sides<16, 128>(sides);
     case 24: return bps_sides<24, 64>(sides);
@@ -82,6 +84,7 @@ cudaError_t launch_lead_f32(const LeadArgs<float>& a, int RT, int sides, dim3 gr
   switch (RT) {
     case 4: return run_sides<4, 256>(a, sides, grid, st);
     case 8: return run_sides<8, 256>(a, sides, grid, st);
+    case 10: return run_sides<10, 128>(a, sides, grid, st);
     case 12: return run_sides<12, 128>(a, sides, grid, st);
     case 16: return run_sides<16, 128>(a, sides, grid, st);
     case 24: return run_sides<24, 64>(a, sides, grid, st);

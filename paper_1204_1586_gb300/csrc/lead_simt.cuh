@@ -53,7 +53,9 @@ struct SimtCfg {
   static constexpr int WC = TK / (32 * TCL);             // L side: column groups
   static constexpr int WR = 8 / WC;                      // L side: row bands
   static constexpr int ROWS_PW = TJ / WR;                // L side: rows per warp
-  static_assert(RT % VEC == 0, "rank tile must be a multiple of the vector width");
+  // FP32 ranks are processed in pairs (fma.rn.f32x2); FP64 ranks in chunks of VEC.
+  static constexpr bool F2 = sizeof(T) == 4;
+  static_assert(F2 ? (RT % 2 == 0) : (RT % VEC == 0), "rank tile must be a multiple of the pair / vector width");
   static_assert(WC >= 1 && 8 % WC == 0, "bad L-side warp grid");
   static_assert(ROWS_PW % VEC == 0, "row band must hold whole chunks");
   static_assert(8 * RT <= STAGES * TK, "R-side reduction must fit in the tile buffers");
@@ -71,6 +73,40 @@ struct SimtCfg {
   // Two CTAs per SM when both shared memory and a 128-register budget allow.
   static constexpr int MIN_BLOCKS = (SIDES != 3 && RT <= 16 && 2 * (smem_bytes + 1024) <= 228 * 1024) ? 2 : 1;
 };
+
+// Paired FP32 arithmetic: two floats in one 64-bit register, one fused
+// multiply-add instruction for both lanes of the pair (sm_100 family).
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// The RT/2 rank pairs of a W row (RT floats, 8-byte aligned), 16 bytes at a
+// time where the pair count allows.
+template <int NP>
+__device__ __forceinline__ void lds_pairs(const float* row, uint64_t (&w)[NP]) {
+  const uint64_t* p = reinterpret_cast<const uint64_t*>(row);
+  if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p + i);
+      w[i] = v.x;
+      w[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) w[i] = p[i];
+  }
+}
 
 // Swizzled position of element (c, j) inside one stage of the tile.
 template <int TJ, int VEC>
@@ -187,23 +223,39 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   }
   __syncthreads();
 
-  T racc[C::NLD][C::VECR][DO_R ? RT : 1];
+  constexpr int NP = RT / 2;  // rank pairs (FP32)
+  T racc[C::NLD][C::VECR][(DO_R && !C::F2) ? RT : 1];  // FP64 accumulators
   T lacc[C::TCL][DO_L ? RT : 1];
+  uint64_t racc2[C::NLD][C::VECR][(DO_R && C::F2) ? NP : 1];
+  uint64_t lacc2[C::TCL][(DO_L && C::F2) ? NP : 1];
   T ss = T(0);  // this thread's sum of y^2 (fixed order); summed in FP64 across threads
   if constexpr (DO_R) {
 #pragma unroll
     for (int m = 0; m < C::NLD; ++m)
 #pragma unroll
-      for (int e = 0; e < C::VECR; ++e)
+      for (int e = 0; e < C::VECR; ++e) {
+        if constexpr (C::F2) {
 #pragma unroll
-        for (int r = 0; r < RT; ++r) racc[m][e][r] = T(0);
+          for (int r = 0; r < NP; ++r) racc2[m][e][r] = 0ull;
+        } else {
+#pragma unroll
+          for (int r = 0; r < RT; ++r) racc[m][e][r] = T(0);
+        }
+      }
   }
-  if constexpr (DO_L) {
+  auto zero_lacc = [&]() {
 #pragma unroll
-    for (int t = 0; t < C::TCL; ++t)
+    for (int t = 0; t < C::TCL; ++t) {
+      if constexpr (C::F2) {
 #pragma unroll
-      for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
-  }
+        for (int r = 0; r < NP; ++r) lacc2[t][r] = 0ull;
+      } else {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
+      }
+    }
+  };
+  if constexpr (DO_L) zero_lacc();
 
   // L-side lane placement.
   const int wr = warp % C::WR, wc = warp / C::WR;
@@ -244,16 +296,32 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
             const int j = lane * C::VECR + 32 * C::VECR * m;
             lds_vec<T, C::VECR>(Yst + tile_off<TJ, VEC>(c, j), y[m]);
           }
-#pragma unroll
-          for (int r4 = 0; r4 < RT; r4 += VEC) {
-            T w[VEC];
-            lds_vec<T, VEC>(Wr + c * RT + r4, w);
+          if constexpr (C::F2) {
+            uint64_t yy[C::NLD][C::VECR];
 #pragma unroll
             for (int m = 0; m < C::NLD; ++m)
 #pragma unroll
-              for (int e = 0; e < C::VECR; ++e)
+              for (int e = 0; e < C::VECR; ++e) yy[m][e] = f2_pack(float(y[m][e]), float(y[m][e]));
+            uint64_t w[NP];
+            lds_pairs<NP>(reinterpret_cast<const float*>(Wr) + c * RT, w);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) racc[m][e][r4 + v] = fma(y[m][e], w[v], racc[m][e][r4 + v]);
+            for (int r = 0; r < NP; ++r)
+#pragma unroll
+              for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+                for (int e = 0; e < C::VECR; ++e) racc2[m][e][r] = f2_fma(yy[m][e], w[r], racc2[m][e][r]);
+          } else {
+#pragma unroll
+            for (int r4 = 0; r4 < RT; r4 += VEC) {
+              T w[VEC];
+              lds_vec<T, VEC>(Wr + c * RT + r4, w);
+#pragma unroll
+              for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+                for (int e = 0; e < C::VECR; ++e)
+#pragma unroll
+                  for (int v = 0; v < VEC; ++v) racc[m][e][r4 + v] = fma(y[m][e], w[v], racc[m][e][r4 + v]);
+            }
           }
           if (do_norm) {
 #pragma unroll
@@ -279,18 +347,41 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
         }
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
+          if constexpr (C::F2) {
+            uint64_t yy[C::TCL];
 #pragma unroll
-          for (int r4 = 0; r4 < RT; r4 += VEC) {
-            T w[VEC];
-            lds_vec<T, VEC>(Wl + (jl + e) * RT + r4, w);
+            for (int t = 0; t < C::TCL; ++t) yy[t] = f2_pack(float(y[t][e]), float(y[t][e]));
+            uint64_t w[NP];
+            lds_pairs<NP>(reinterpret_cast<const float*>(Wl) + (jl + e) * RT, w);
 #pragma unroll
-            for (int t = 0; t < C::TCL; ++t)
+            for (int r = 0; r < NP; ++r)
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) lacc[t][r4 + v] = fma(y[t][e], w[v], lacc[t][r4 + v]);
+              for (int t = 0; t < C::TCL; ++t) lacc2[t][r] = f2_fma(yy[t], w[r], lacc2[t][r]);
+          } else {
+#pragma unroll
+            for (int r4 = 0; r4 < RT; r4 += VEC) {
+              T w[VEC];
+              lds_vec<T, VEC>(Wl + (jl + e) * RT + r4, w);
+#pragma unroll
+              for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) lacc[t][r4 + v] = fma(y[t][e], w[v], lacc[t][r4 + v]);
+            }
           }
         }
       }
       if (rt == nrt - 1) {
+        if constexpr (C::F2) {
+#pragma unroll
+          for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+              float a0, a1;
+              f2_unpack(lacc2[t][r], a0, a1);
+              lacc[t][2 * r] = a0;
+              lacc[t][2 * r + 1] = a1;
+            }
+        }
         // The chunk's columns are complete over this J-block: sum the row bands.
         if constexpr (C::WR > 1) {
           T* red = C::RED_ALIAS ? Yst : red_sep;
@@ -317,10 +408,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
               if (r0 + r < R && cg < kend) a.Lpart[(int64_t(jb) * R + r0 + r) * K + cg] = lacc[t][r];
           }
         }
-#pragma unroll
-        for (int t = 0; t < C::TCL; ++t)
-#pragma unroll
-          for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
+        zero_lacc();
       }
     }
   }
@@ -338,7 +426,15 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       for (int r = 0; r < RT; ++r) {
         T v[C::VECR];
 #pragma unroll
-        for (int e = 0; e < C::VECR; ++e) v[e] = racc[m][e][r];
+        for (int e = 0; e < C::VECR; ++e) {
+          if constexpr (C::F2) {
+            float a0, a1;
+            f2_unpack(racc2[m][e][r / 2], a0, a1);
+            v[e] = (r & 1) ? a1 : a0;
+          } else {
+            v[e] = racc[m][e][r];
+          }
+        }
         sts_vec<T, C::VECR>(redR + (size_t(warp) * RT + r) * TJ + j, v);
       }
     }
