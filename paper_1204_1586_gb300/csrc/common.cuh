@@ -47,6 +47,19 @@ struct KrRows {
     if (Q != nullptr) v *= Q[q + ldq * r];
     return v;
   }
+  // Split form for software pipelining: fetch() issues the two loads, the
+  // caller multiplies the pair later.
+  __device__ __forceinline__ void fetch(uint32_t idx, int r, T& fa, T& fq) const {
+    if (A == nullptr) {
+      fa = T(1);
+      fq = T(1);
+      return;
+    }
+    const uint32_t q = d.div(idx);
+    const uint32_t i = idx - q * d.d;
+    fa = A[i + int64_t(d.d) * r];
+    fq = (Q != nullptr) ? Q[q + ldq * r] : T(1);
+  }
 };
 
 // Geometry of one leading contraction (Algorithm 2 steps 4/7):

@@ -218,8 +218,68 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       dst[f] = (jg < J && r0 + r < R) ? a.wl.at(uint32_t(jg), r0 + r) : T(0);
     }
   };
+  // Register staging of one stage's Khatri-Rao entries (f = tid + NT*u).
+  constexpr int EWR = DO_R ? (TK * RT + NT - 1) / NT : 1;
+  constexpr int EWL = (DO_L && !DO_R) ? (TJ * RT + NT - 1) / NT : 1;
+  T pwa[EWR], pwq[EWR], pla[EWL], plq[EWL];
+  auto fetch_wr = [&](int it2) {
+    const int64_t cb = kbeg + int64_t(it2 / nrt) * TK;
+#pragma unroll
+    for (int u = 0; u < EWR; ++u) {
+      const int f = tid + NT * u;
+      const int c = f / RT, r = f % RT;
+      const int64_t cg = cb + c;
+      if (it2 < nst && f < TK * RT && cg < kend && r0 + r < R) {
+        a.wr.fetch(uint32_t(cg), r0 + r, pwa[u], pwq[u]);
+      } else {
+        pwa[u] = T(0);
+        pwq[u] = T(0);
+      }
+    }
+  };
+  auto store_wr = [&](int it2) {
+    T* Wr = WRs + size_t(it2 & 1) * TK * RT;
+#pragma unroll
+    for (int u = 0; u < EWR; ++u) {
+      const int f = tid + NT * u;
+      if (f < TK * RT) Wr[f] = pwa[u] * pwq[u];
+    }
+  };
+  auto fetch_wl = [&](int it2) {
+    const int64_t j0 = jblk + int64_t(it2 % nrt) * TJ;
+#pragma unroll
+    for (int u = 0; u < EWL; ++u) {
+      const int f = tid + NT * u;
+      const int j = f / RT, r = f % RT;
+      const int64_t jg = j0 + j;
+      if (it2 < nst && f < TJ * RT && jg < J && r0 + r < R) {
+        a.wl.fetch(uint32_t(jg), r0 + r, pla[u], plq[u]);
+      } else {
+        pla[u] = T(0);
+        plq[u] = T(0);
+      }
+    }
+  };
+  auto store_wl = [&](int it2) {
+    T* Wl = WLs + size_t(it2 & 1) * TJ * RT;
+#pragma unroll
+    for (int u = 0; u < EWL; ++u) {
+      const int f = tid + NT * u;
+      if (f < TJ * RT) Wl[f] = pla[u] * plq[u];
+    }
+  };
   if constexpr (DO_L) {
     if (nrt == 1) gen_wl(WLs, 0);
+  }
+  if constexpr (DO_R) {
+    fetch_wr(0);
+    store_wr(0);
+  }
+  if constexpr (DO_L && !DO_R) {
+    if (nrt > 1) {
+      fetch_wl(0);
+      store_wl(0);
+    }
   }
   __syncthreads();
 
@@ -269,19 +329,14 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     cp_async_wait<STAGES - 2>();
     const int ci = it / nrt, rt = it % nrt;
     const int64_t cbase = kbeg + int64_t(ci) * TK;
-    if constexpr (DO_R) {
-      T* Wr = WRs + size_t(it & 1) * TK * RT;
-      for (int f = tid; f < TK * RT; f += NT) {
-        const int c = f / RT, r = f % RT;
-        const int64_t cg = cbase + c;
-        Wr[f] = (cg < kend && r0 + r < R) ? a.wr.at(uint32_t(cg), r0 + r) : T(0);
-      }
-    }
-    if constexpr (DO_L && !DO_R) {
-      if (nrt > 1) gen_wl(WLs + size_t(it & 1) * TJ * RT, rt);
-    }
     __syncthreads();
     issue(it + STAGES - 1);
+    // Khatri-Rao rows of the next stage: loads now, products stored after this
+    // stage's arithmetic (into the buffer the previous stage used).
+    if constexpr (DO_R) fetch_wr(it + 1);
+    if constexpr (DO_L && !DO_R) {
+      if (nrt > 1) fetch_wl(it + 1);
+    }
 
     T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
     if constexpr (DO_R) {
@@ -410,6 +465,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
         }
         zero_lacc();
       }
+    }
+    if constexpr (DO_R) {
+      if (it + 1 < nst) store_wr(it + 1);
+    }
+    if constexpr (DO_L && !DO_R) {
+      if (nrt > 1 && it + 1 < nst) store_wl(it + 1);
     }
   }
 
