@@ -11,6 +11,8 @@
 #include "chain.cuh"
 #include "common.cuh"
 #include "lead_dispatch.cuh"
+#include "lead_tc.cuh"
+#include "lead_tc_dispatch.cuh"
 
 using namespace cpg;
 
@@ -29,6 +31,8 @@ struct LeadTiming {
   bool made = false;
 };
 LeadTiming g_timing;
+// Device status word of the current call's workspace (for kernels that report timeouts).
+thread_local int* g_status_ptr = nullptr;
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -83,6 +87,9 @@ bool is_f64(int prec) { return prec == CPG_FP64; }
 
 // ---- leading-pass plan ----------------------------------------------------------
 struct LeadPlan {
+  bool tc = false;  // tensor-core kernel (split BF16 products)
+  int tc_prec = 0;  // 0 = BF16x3, 1 = BF16
+  int RTP = 0;      // tensor-core rank tile
   int k = 0, sides = 0;
   int64_t J = 0, K = 0;
   int RTmax = 0, groups = 0;   // rank groups of at most RTmax columns
@@ -94,7 +101,62 @@ struct LeadPlan {
 
 SimtShape shape_for(int prec, int r) { return is_f64(prec) ? simt_shape_f64(r) : simt_shape_f32(r); }
 
+bool is_tc_prec(int prec) { return prec == CPG_BF16X3 || prec == CPG_BF16; }
+
+// Grid over (J-blocks, K-splits): the K-split count that best fills `slots`
+// resident CTAs, discounting CTAs that run only a few stages.
+void choose_ksplit(LeadPlan& p, int slots) {
+  const int64_t chunks = (p.K + p.TK - 1) / p.TK;
+  double best = -1.0;
+  int best_ks = 1;
+  const int64_t max_ks = std::min<int64_t>(chunks, 4096);
+  for (int64_t ks = 1; ks <= max_ks; ++ks) {
+    const int64_t per = (chunks + ks - 1) / ks;
+    const int64_t nks = (chunks + per - 1) / per;
+    if (nks != ks) continue;
+    const int64_t units = int64_t(p.nJb) * nks;
+    if (units > 65535LL * 64) break;
+    const int64_t waves = (units + slots - 1) / slots;
+    const double eff = double(units) / double(waves * slots);
+    const double stages = double(per * p.nrt);
+    const double score = eff * stages / (stages + 1.5);
+    if (score > best + 1e-9) {
+      best = score;
+      best_ks = int(nks);
+    }
+  }
+  p.nKs = best_ks;
+  p.Kc = ((chunks + p.nKs - 1) / p.nKs) * p.TK;
+}
+
+LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
+  LeadPlan p;
+  p.tc = true;
+  p.tc_prec = (prec == CPG_BF16X3) ? 0 : 1;
+  p.k = k;
+  p.sides = sides;
+  p.J = prod(s, 0, k);
+  p.K = prod(s, k, s.N);
+  p.RTmax = 64;
+  p.groups = (R + p.RTmax - 1) / p.RTmax;
+  p.RTP = tc_rank_tile(std::min(R, p.RTmax));
+  p.TJ = 128;
+  p.TK = 128;
+  const int64_t tiles = (p.J + 127) / 128;
+  const int cap = std::min(tc_max_nrt(p.RTP, sides, p.tc_prec), sides == 2 ? 16 : 8);
+  p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
+  p.nJb = int((p.J + 128LL * p.nrt - 1) / (128LL * p.nrt));
+  choose_ksplit(p, num_sms());
+  p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
+  p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
+  return p;
+}
+
 LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
+  // Split-BF16 forms run on the tensor cores when rows are whole 16-byte
+  // chunks (a TMA requirement); otherwise the FP32 CUDA-core kernel runs.
+  if (is_tc_prec(prec) && (prod(s, 0, k) % 4) == 0) return plan_lead_tc(s, R, k, sides, prec);
+  if (is_tc_prec(prec)) prec = CPG_FP32;
   LeadPlan p;
   p.k = k;
   p.sides = sides;
@@ -375,6 +437,37 @@ KrRows<T> make_rows(const Shape& s, const void* const* A, int R, int mb, int me,
 template <typename T>
 cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, const LeadPlan& p, T* Rpart, T* Lpart,
                      double* normpart, int prec, const LeadTabs<T>& tabs, cudaStream_t st) {
+  if constexpr (std::is_same_v<T, float>) {
+    if (p.tc) {
+      TcArgs a{};
+      a.J = p.J;
+      a.K = p.K;
+      a.R = R;
+      if (p.sides & 2) a.wl = make_rows<float>(s, A, R, 0, p.k, tabs.qL, st);
+      if (p.sides & 1) a.wr = make_rows<float>(s, A, R, p.k, s.N, tabs.qR, st);
+      a.Kc = p.Kc;
+      a.nrt = p.nrt;
+      a.Rpart = Rpart;
+      a.Lpart = Lpart;
+      a.status = g_status_ptr;
+      for (int g = 0; g < p.groups; ++g) {
+        a.r0 = g * p.RTmax;
+        a.normpart = (g == 0) ? normpart : nullptr;
+        ++g_launches;
+        const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
+        const int slot = g_timing.n;
+        if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
+        cudaError_t e = launch_lead_tc(Y, a, p.RTP, p.sides, p.tc_prec, dim3(p.nJb, p.nKs), st);
+        if (timed) {
+          cudaEventRecord(g_timing.ev[2 * slot + 1], st);
+          g_timing.sides[slot] = p.sides;
+          g_timing.n = slot + 1;
+        }
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
   LeadArgs<T> a{};
   a.Y = Y;
   a.J = p.J;
@@ -463,7 +556,7 @@ cpg_status common_checks(const cpg_opts* opts, Shape& s, const int64_t* I, int N
   if (st != CPG_OK) return st;
   if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
   if (opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return CPG_ERR_ARG;
-  if (opts->precision != CPG_FP32 && opts->precision != CPG_FP64) return CPG_ERR_UNSUPPORTED;
+  if (opts->precision == CPG_TF32X3) return CPG_ERR_UNSUPPORTED;
   return CPG_OK;
 }
 
@@ -490,6 +583,8 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
   if (!lead_fits(pr) || !lead_fits(pl)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  if ((pr.tc || pl.tc) && !tc_eligible(reinterpret_cast<const float*>(Y), pr.J)) return CPG_ERR_UNSUPPORTED;
+  g_status_ptr = w.h.status;
 
   // Steps 4 and 7: R^(k) and L^(k+1) from one read of Y (or two passes).
   cudaError_t e = run_lead<T>(s, Y, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, w.tabs, st);
@@ -554,6 +649,8 @@ cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, 
   ModeWs<T> w = carve_mode<T>(o->workspace, s, R, n, rt, &need);
   if (!lead_fits(rt.lead)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  if (rt.lead.tc && !tc_eligible(reinterpret_cast<const float*>(Y), rt.lead.J)) return CPG_ERR_UNSUPPORTED;
+  g_status_ptr = w.h.status;
   const LeadPlan& p = rt.lead;
   if (rt.right) {
     // R^(n) = Y_(1:n) (KR over modes > n) (eq. 3.10), then eq. 3.12.
@@ -584,6 +681,8 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
   if (!lead_fits(lr) || !lead_fits(ll)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  if ((lr.tc || ll.tc) && !tc_eligible(reinterpret_cast<const float*>(Y), lr.J)) return CPG_ERR_UNSUPPORTED;
+  g_status_ptr = w.h.status;
   const void* const* Ac = const_cast<const void* const*>(A);
 
   constexpr bool kDf = std::is_same_v<T, float>;

@@ -1,0 +1,87 @@
+// Host side of the tensor-core leading contraction: TMA tensor map of Y and
+// the kernel instances (rank tile 16 / 32 / 64, sides, BF16x3 or BF16).
+#include <cudaTypedefs.h>
+
+#include "lead_tc.cuh"
+#include "lead_tc_dispatch.cuh"
+
+namespace cpg {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Y as a 2-D tensor [K][J] (J contiguous); one box = 128 rows x 64 columns.
+bool make_y_map(CUtensorMap* m, const float* Y, int64_t J, int64_t K) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(J), cuuint64_t(K)};
+  const cuuint64_t strides[1] = {cuuint64_t(J) * sizeof(float)};
+  const cuuint32_t box[2] = {128, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Y), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int RTP, int SIDES, int PREC>
+cudaError_t run(const CUtensorMap& m, const TcArgs& a, dim3 grid, cudaStream_t st) {
+  using C = TcCfg<RTP, SIDES, PREC>;
+  auto kern = lead_tc_kernel<RTP, SIDES, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, C::NT, C::smem_bytes, st>>>(m, a);
+  return cudaGetLastError();
+}
+
+template <int RTP, int PREC>
+cudaError_t run_sides(const CUtensorMap& m, const TcArgs& a, int sides, dim3 grid, cudaStream_t st) {
+  switch (sides) {
+    case 1: return run<RTP, 1, PREC>(m, a, grid, st);
+    case 2: return run<RTP, 2, PREC>(m, a, grid, st);
+    case 3: return run<RTP, 3, PREC>(m, a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int RTP>
+cudaError_t run_prec(const CUtensorMap& m, const TcArgs& a, int sides, int prec, dim3 grid, cudaStream_t st) {
+  return prec == 0 ? run_sides<RTP, 0>(m, a, sides, grid, st) : run_sides<RTP, 1>(m, a, sides, grid, st);
+}
+
+}  // namespace
+
+int tc_rank_tile(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : 64; }
+
+int tc_max_nrt(int RTP, int sides, int prec) {
+  const int nw = (prec == 0) ? 2 * RTP : RTP;
+  if (sides == 2) return 1 << 20;     // only the step-7 accumulator lives in tensor memory
+  return sides == 1 ? 512 / nw : 512 / nw - 1;
+}
+
+bool tc_eligible(const float* Y, int64_t J) {
+  return (reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (J % 4) == 0 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {
+  CUtensorMap m;
+  if (!make_y_map(&m, Y, a.J, a.K)) return cudaErrorInvalidValue;
+  switch (RTP) {
+    case 16: return run_prec<16>(m, a, sides, prec, grid, st);
+    case 32: return run_prec<32>(m, a, sides, prec, grid, st);
+    case 64: return run_prec<64>(m, a, sides, prec, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cpg

@@ -1,0 +1,346 @@
+// Leading contractions of Algorithm 2 (steps 4 and 7) on the 5th-generation
+// tensor cores (tcgen05), with split-BF16 operands and FP32 accumulation.
+//
+// Y is the J x K column-major matrix reshape(Y, [J_k, K_k]) (eq. 2.3); one
+// CTA owns a J-block of nrt row tiles of 128 rows and a range of columns, and
+// walks it in super-stages of (128 columns) x (one row tile):
+//
+//   TMA      two 128 x 64 FP32 boxes per super-stage into shared memory
+//            (NBUF fp32 buffers, prefetched NBUF/2 super-stages ahead);
+//   convert  all threads split y = hi + lo (BF16 round-to-nearest each) and
+//            write hi and lo as one 128 x 128 tile of 1 KB atoms
+//            [column group of 8][row half][8 columns][64 rows, 128-byte swizzle]
+//            which is at once the MN-major A operand of step 4 (M = rows,
+//            K = columns) and the K-major A operand of step 7 (M = columns,
+//            K = rows);
+//   KR rows  the Khatri-Rao rows W_R (columns) and W_L (rows) of eq. 3.9/3.10
+//            are generated per tile (factor row x Kronecker-table entry) and
+//            split into BF16 hi / lo rows of a K-major B operand;
+//   MMA      one thread issues tcgen05.mma (M = 128, K = 16 per step):
+//            step 4: D_R[row tile] += A_hi [W_hi | W_lo] + A_lo W_hi
+//            step 7: D_L           += A_hi [W_hi | W_lo] + A_lo W_hi
+//            (the BF16x3 split product; the plain BF16 form keeps A_hi W_hi);
+//            D_R of every row tile of the block and D_L live in tensor memory;
+//   epilogue D_L is read back (tcgen05.ld) after each column chunk's last row
+//            tile; D_R after the CTA's last column.  Outputs are the same
+//            deterministic partial sums as the CUDA-core kernel.
+//
+// Every mbarrier wait is bounded; on expiry the CTA records CPG_ERR_TIMEOUT in
+// the status word, waits (bounded) for its own operations, frees its tensor
+// memory and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace cpg {
+
+struct TcArgs {
+  int64_t J, K;
+  int R, r0;
+  KrRows<float> wl, wr;
+  int64_t Kc;      // columns per CTA (multiple of 128)
+  int nrt;         // row tiles per J-block
+  float* Rpart;    // [nKs][R][J]
+  float* Lpart;    // [nJb][R][K]
+  double* normpart;  // [nJb*nKs] partial sums of y^2 (R side only), or nullptr
+  int* status;
+};
+
+template <int RTP, int SIDES, int PREC>
+struct TcCfg {
+  static constexpr bool DO_R = (SIDES & 1) != 0;
+  static constexpr bool DO_L = (SIDES & 2) != 0;
+  static constexpr bool X3 = PREC == 0;                 // BF16x3; else plain BF16
+  static constexpr int NT = 256;
+  static constexpr int NBUF = (RTP >= 64) ? 2 : 4;     // fp32 128 x 64 boxes
+  static constexpr int NPAIR = NBUF / 2;
+  static constexpr int NW = X3 ? 2 * RTP : RTP;         // B rows (hi, then lo)
+  static constexpr uint32_t F32_BYTES = 128 * 64 * 4;   // one TMA box
+  static constexpr uint32_t SPLIT_BYTES = 128 * 128 * 2;
+  static constexpr uint32_t W_BYTES = uint32_t(NW) * 128 * 2;
+  static constexpr uint32_t OFF_F32 = 0;
+  static constexpr uint32_t OFF_HI = OFF_F32 + NBUF * F32_BYTES;
+  static constexpr uint32_t OFF_LO = OFF_HI + SPLIT_BYTES;
+  static constexpr uint32_t OFF_WR = OFF_LO + (X3 ? SPLIT_BYTES : 0);
+  static constexpr uint32_t OFF_WL = OFF_WR + (DO_R ? W_BYTES : 0);
+  static constexpr uint32_t OFF_END = OFF_WL + (DO_L ? W_BYTES : 0);
+  static constexpr size_t smem_bytes = OFF_END + 1024;  // + alignment slack
+  static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
+  static_assert(RTP % 16 == 0 && RTP <= 64, "MMA N must be a multiple of 16");
+  static constexpr int max_nrt = DO_R && DO_L ? (512 / (2 * RTP)) - 1 : 1;
+};
+
+// Byte offset of element (row j, column c) of the split tile.
+__device__ __forceinline__ uint32_t split_off(int j, int c) {
+  const int atom = (c >> 3) * 2 + (j >> 6);
+  const int row = c & 7, chunk = ((j & 63) >> 3) ^ row;
+  return uint32_t(atom * 1024 + row * 128 + chunk * 16 + (j & 7) * 2);
+}
+// Byte offset of element (B row n, k) of a W tile (K-major, 2 K atoms per 8 rows).
+__device__ __forceinline__ uint32_t wtile_off(int n, int k) {
+  const int atom = (n >> 3) * 2 + (k >> 6);
+  const int row = n & 7, chunk = ((k & 63) >> 3) ^ row;
+  return uint32_t(atom * 1024 + row * 128 + chunk * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// hi = bf16(x), lo = bf16(x - hi) for 8 values; packed 16 bytes each.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+  float h[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    h[e] = __bfloat162float(__float2bfloat16_rn(x[e]));
+    l[e] = x[e] - h[e];
+  }
+  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+}
+
+template <int RTP, int SIDES, int PREC>
+__global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
+  using C = TcCfg<RTP, SIDES, PREC>;
+  constexpr bool DO_R = C::DO_R, DO_L = C::DO_L, X3 = C::X3;
+  constexpr int NT = C::NT;
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t bar_full[C::NBUF];
+  __shared__ uint64_t bar_mma;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t J = a.J, K = a.K;
+  const int R = a.R, r0 = a.r0;
+  const int nrt = a.nrt;
+  const int jb = blockIdx.x, ks = blockIdx.y;
+  const int64_t jblk = int64_t(jb) * 128 * nrt;
+  const int64_t kbeg = int64_t(ks) * a.Kc;
+  const int64_t kend = (kbeg + a.Kc < K) ? (kbeg + a.Kc) : K;
+  const int nchunk = int((kend - kbeg + 127) / 128);
+  const int nss = nchunk * nrt;
+  const int tcols_needed = (DO_R ? nrt : 0) * C::NW + (DO_L ? C::NW : 0);
+  uint32_t tcols = 32;
+  while (tcols < uint32_t(tcols_needed)) tcols <<= 1;
+  const uint32_t colL = (DO_R ? nrt : 0) * C::NW;
+
+  if (tid == 0) {
+    for (int b = 0; b < C::NBUF; ++b) tc::mbar_init(&bar_full[b], 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, tcols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  int last_issued = 0;  // super-stages whose TMA thread 0 has issued
+  int mma_issued = 0;   // super-stages whose MMAs thread 0 has issued
+  auto issue_tma = [&](int ss) {  // thread 0 only
+    last_issued = ss + 1;
+    const int pair = ss % C::NPAIR;
+    const int64_t cb = kbeg + int64_t(ss / nrt) * 128;
+    const int64_t j0 = jblk + int64_t(ss % nrt) * 128;
+    for (int h = 0; h < 2; ++h) {
+      uint64_t* bar = &bar_full[2 * pair + h];
+      tc::mbar_arrive_expect_tx(bar, C::F32_BYTES);
+      tc::tma_load_2d(sm + C::OFF_F32 + (2 * pair + h) * C::F32_BYTES, &tmap, int(j0), int(cb + 64 * h), bar);
+    }
+  };
+  if (tid == 0) {
+    for (int ss = 0; ss < C::NPAIR && ss < nss; ++ss) issue_tma(ss);
+  }
+
+  // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).
+  auto gen_w = [&](unsigned char* tile, const KrRows<float>& kr, int64_t base, int64_t limit) {
+    for (int task = tid; task < RTP * 16; task += NT) {
+      const int n = task >> 4, kq = task & 15;
+      float w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t g = base + kq * 8 + e;
+        w[e] = (g < limit && r0 + n < R) ? kr.at(uint32_t(g), r0 + n) : 0.f;
+      }
+      uint4 hi, lo;
+      split8(w, hi, lo);
+      *reinterpret_cast<uint4*>(tile + wtile_off(n, kq * 8)) = hi;
+      if constexpr (X3) *reinterpret_cast<uint4*>(tile + wtile_off(RTP + n, kq * 8)) = lo;
+    }
+  };
+
+  // L epilogue: D_L rows are the chunk's 128 columns.
+  auto epilogue_L = [&](int q) {
+    if (warp < 4) {
+      const int64_t c = kbeg + int64_t(q) * 128 + 32 * warp + lane;
+      float v[16], u[16];
+#pragma unroll
+      for (int r16 = 0; r16 < RTP; r16 += 16) {
+        tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + colL + r16, v);
+        if constexpr (X3) tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + colL + RTP + r16, u);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = r0 + r16 + i;
+          const float val = X3 ? v[i] + u[i] : v[i];
+          if (r < R && c < kend) a.Lpart[(int64_t(jb) * R + r) * K + c] = val;
+        }
+      }
+    }
+  };
+
+  const bool do_norm = DO_R && a.normpart != nullptr;
+  float ysq = 0.f;  // this thread's share of sum y^2 (rows beyond J are zero)
+  bool ok = true;
+  for (int ss = 0; ss < nss; ++ss) {
+    const int q = ss / nrt, rt = ss % nrt, pair = ss % C::NPAIR;
+    const uint32_t par = uint32_t(ss / C::NPAIR) & 1u;
+    if (!tc::mbar_wait(&bar_full[2 * pair], par) || !tc::mbar_wait(&bar_full[2 * pair + 1], par)) ok = false;
+    if (ss > 0 && !tc::mbar_wait(&bar_mma, uint32_t(ss - 1) & 1u)) ok = false;
+    if (!ok) {
+      atomicExch(&abort_flag, 1);
+    }
+    tc::tc_fence_after();
+    __syncthreads();
+    if (abort_flag) {
+      ok = false;
+      break;
+    }
+    if constexpr (DO_L) {
+      if (ss > 0 && (ss - 1) % nrt == nrt - 1) epilogue_L(q - 1);
+    }
+    // Split the two fp32 boxes into the BF16 hi / lo tile.
+    {
+      const int64_t cb0 = kbeg + int64_t(q) * 128;
+      const unsigned char* f32 = sm + C::OFF_F32 + (2 * pair) * C::F32_BYTES;
+      for (int task = tid; task < 128 * 16; task += NT) {
+        const int c = task >> 4, jq = task & 15;
+        const float* src = reinterpret_cast<const float*>(f32 + (c >> 6) * C::F32_BYTES + (c & 63) * 512 + jq * 32);
+        const float4 p0 = reinterpret_cast<const float4*>(src)[0];
+        const float4 p1 = reinterpret_cast<const float4*>(src)[1];
+        const float x[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        if constexpr (DO_R) {
+          if (do_norm && cb0 + c < kend) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) ysq = fmaf(x[e], x[e], ysq);
+          }
+        }
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        const uint32_t off = split_off(jq * 8, c);
+        *reinterpret_cast<uint4*>(sm + C::OFF_HI + off) = hi;
+        if constexpr (X3) *reinterpret_cast<uint4*>(sm + C::OFF_LO + off) = lo;
+      }
+    }
+    const int64_t cb = kbeg + int64_t(q) * 128;
+    const int64_t j0 = jblk + int64_t(rt) * 128;
+    if constexpr (DO_R) {
+      if (rt == 0) gen_w(sm + C::OFF_WR, a.wr, cb, kend);
+    }
+    if constexpr (DO_L) {
+      if (nrt > 1 || ss == 0) gen_w(sm + C::OFF_WL, a.wl, j0, J);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::tc_fence_after();
+      if (ss + C::NPAIR < nss) issue_tma(ss + C::NPAIR);
+      const uint32_t hi0 = tc::smem_addr(sm + C::OFF_HI), lo0 = tc::smem_addr(sm + C::OFF_LO);
+      if constexpr (DO_R) {
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR);
+        const uint32_t d = tbase + uint32_t(rt) * C::NW;
+        for (int s = 0; s < 8; ++s) {
+          const uint64_t bd = tc::smem_desc_sw128(w0 + (s >> 2) * 1024 + (s & 3) * 32, 16, 2048);
+          tc::mma_bf16(d, tc::smem_desc_sw128(hi0 + s * 4096, 1024, 2048), bd,
+                       tc::idesc_bf16_f32(128, C::NW, 1, 0), (q > 0 || s > 0) ? 1u : 0u);
+          if constexpr (X3)
+            tc::mma_bf16(d, tc::smem_desc_sw128(lo0 + s * 4096, 1024, 2048), bd, tc::idesc_bf16_f32(128, RTP, 1, 0), 1u);
+        }
+      }
+      if constexpr (DO_L) {
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL);
+        const uint32_t d = tbase + colL;
+        for (int s = 0; s < 8; ++s) {
+          const uint32_t koff = (s >> 2) * 1024 + (s & 3) * 32;
+          const uint64_t bd = tc::smem_desc_sw128(w0 + koff, 16, 2048);
+          tc::mma_bf16(d, tc::smem_desc_sw128(hi0 + koff, 16, 2048), bd, tc::idesc_bf16_f32(128, C::NW, 0, 0),
+                       (rt > 0 || s > 0) ? 1u : 0u);
+          if constexpr (X3)
+            tc::mma_bf16(d, tc::smem_desc_sw128(lo0 + koff, 16, 2048), bd, tc::idesc_bf16_f32(128, RTP, 0, 0), 1u);
+        }
+      }
+      tc::mma_commit(&bar_mma);
+      mma_issued = ss + 1;
+    }
+  }
+
+  __syncthreads();  // every thread has left the loop
+  bool aborted = abort_flag != 0;
+  if (!aborted && nss > 0) {
+    if (!tc::mbar_wait(&bar_mma, uint32_t(nss - 1) & 1u)) atomicExch(&abort_flag, 1);
+    tc::tc_fence_after();
+    __syncthreads();
+    aborted = abort_flag != 0;
+    if (!aborted) {
+      if constexpr (DO_L) epilogue_L(nchunk - 1);
+      if constexpr (DO_R) {
+        if (warp < 4) {
+          for (int rt = 0; rt < nrt; ++rt) {
+            const int64_t j = jblk + int64_t(rt) * 128 + 32 * warp + lane;
+            float v[16], u[16];
+#pragma unroll
+            for (int r16 = 0; r16 < RTP; r16 += 16) {
+              tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + uint32_t(rt) * C::NW + r16, v);
+              if constexpr (X3) tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + uint32_t(rt) * C::NW + RTP + r16, u);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int r = r0 + r16 + i;
+                const float val = X3 ? v[i] + u[i] : v[i];
+                if (r < R && j < J) a.Rpart[(int64_t(ks) * R + r) * J + j] = val;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  if constexpr (DO_R) {
+    if (do_norm) {
+      double sd = double(ysq);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+      __shared__ double wsum[8];
+      if (lane == 0) wsum[warp] = sd;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += wsum[w];
+        a.normpart[int64_t(ks) * gridDim.x + jb] = t;
+      }
+    }
+  }
+  if (aborted && tid == 0) {
+    atomicCAS(a.status, 0, int(CPG_ERR_TIMEOUT));
+    // Let this CTA's own copies and MMAs drain (bounded) before its memory is released.
+    for (int ss = 0; ss < last_issued; ++ss) {
+      const int pair = ss % C::NPAIR;
+      const uint32_t par = uint32_t(ss / C::NPAIR) & 1u;
+      tc::mbar_wait(&bar_full[2 * pair], par, 1u << 16);
+      tc::mbar_wait(&bar_full[2 * pair + 1], par, 1u << 16);
+    }
+    tc::mbar_wait(&bar_mma, uint32_t(mma_issued - 1) & 1u, 1u << 20);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, tcols);
+}
+
+}  // namespace cpg

@@ -12,7 +12,7 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "fp64": 1e-12}
+TOL = {"fp32": 1e-5, "fp64": 1e-12, "bf16x3": 1e-5, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -62,6 +62,16 @@ GRAD_CASES = [
     ([13, 7, 9, 11], 8, "fp64"),
     ([21, 22, 23], 16, "fp64"),
     ([5, 6, 7], 20, "fp64"),            # two rank groups in FP64
+    # split-BF16 forms on the tensor cores (J * 4 a multiple of 16)
+    ([24, 20, 30, 17], 12, "bf16x3"),   # k=2, J=480: ragged row tile and column chunk
+    ([100, 100, 100], 20, "bf16x3"),    # k=1, J=100, rank tile 32
+    ([64, 64, 64, 4], 3, "bf16x3"),
+    ([32, 16, 20, 24, 10], 10, "bf16x3"),
+    ([12, 11, 10, 9], 64, "bf16x3"),    # rank tile 64 (J=132)
+    ([9, 10, 11], 70, "bf16x3"),        # J=9: rows not 16-byte multiples -> FP32 CUDA-core path
+    ([20, 12, 40, 36], 33, "bf16x3"),   # rank tile 64, R not a multiple of 16
+    ([40, 36, 28, 20], 16, "bf16"),
+    ([100, 100, 100], 10, "bf16"),
 ]
 
 
@@ -92,7 +102,8 @@ def test_gradient_all_split_override(cg, split):
 
 @pytest.mark.parametrize("I,R,prec", [([30, 40, 50], 5, "fp32"), ([11, 9, 13, 7, 5], 9, "fp32"),
                                       ([200, 3, 4], 6, "fp32"), ([3, 4, 200], 6, "fp32"),
-                                      ([13, 7, 9, 11], 8, "fp64")])
+                                      ([13, 7, 9, 11], 8, "fp64"), ([40, 12, 8, 20], 8, "bf16x3"),
+                                      ([4, 8, 300], 6, "bf16x3")])
 def test_gradient_mode(cg, I, R, prec):
     y, A, dt = inputs(I, R, prec, seed=5)
     Y = torch.from_numpy(y).cuda()
@@ -130,14 +141,15 @@ def test_gradient_deterministic(cg):
 
 
 @pytest.mark.slow
-def test_gradient_full_size_sampled(cg):
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_gradient_full_size_sampled(cg, prec):
     """The 4-D 100^4, R = 10 workload in the benchmark's launch configuration;
     sampled entries g_r^(n)[i] checked one by one with the oracle (eq. 3.2)."""
     p = cpsynth.workload("cp4d_100_r10_fp32")
     I, R = p.I, p.R
     Y = torch.from_numpy(p.y).cuda()
     Ad = [dev_factor(a, np.float32) for a in p.init]
-    G = [g.double().cpu().numpy() for g in cg.cp_gradient_all(Y, I, Ad)]
+    G = [g.double().cpu().numpy() for g in cg.cp_gradient_all(Y, I, Ad, precision=prec)]
     rng = np.random.default_rng(0)
     for n in range(len(I)):
         for _ in range(5):
@@ -147,14 +159,15 @@ def test_gradient_full_size_sampled(cg):
             assert abs(G[n][i, r] - want) <= 1e-5 * max(abs(want), scale), (n, i, r)
     # one ALS sweep from the same start: fit against the oracle's fit
     Ad = [dev_factor(a, np.float32) for a in p.init]
-    lam, fit = cg.cp_als_iter(Y, I, Ad, 1)
+    lam, fit = cg.cp_als_iter(Y, I, Ad, 1, precision=prec)
     torch.cuda.synchronize()
     tr = oracle.cp_als(p.y, I, p.init, iters=1)
     assert abs(fit.cpu().numpy()[0] - tr.fits[0]) <= 1e-5
 
 
 @pytest.mark.parametrize("I,R,prec,iters", [([30, 40, 50], 5, "fp64", 10), ([24, 20, 30, 17], 6, "fp32", 6),
-                                            ([12, 10, 8, 9, 7], 4, "fp32", 5), ([40, 30], 3, "fp32", 8)])
+                                            ([12, 10, 8, 9, 7], 4, "fp32", 5), ([40, 30], 3, "fp32", 8),
+                                            ([24, 20, 30, 17], 6, "bf16x3", 6), ([40, 36, 28], 5, "bf16x3", 5)])
 def test_als_matches_oracle(cg, I, R, prec, iters):
     dt = np.float64 if prec == "fp64" else np.float32
     p = cpsynth.make_problem(I, R, snr_db=20.0, seed=11, dtype=dt)
