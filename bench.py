@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16"],
+                    help="arithmetic of the leading contraction (Algorithm 2 steps 4/7)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run for ncu: warm-up and timed steps only, no e2e, checks or CPU baseline")
     args = ap.parse_args()
@@ -244,11 +246,13 @@ def main():
     ws = cg.Workspace(dev)
     stream = torch.cuda.current_stream()
 
+    prec = args.precision
+
     def step(Yd):
-        cg.cp_gradient_all(Yd, I, A0, G, workspace=ws)
+        cg.cp_gradient_all(Yd, I, A0, G, workspace=ws, precision=prec)
         for a, a0 in zip(A, A0):
             a.copy_(a0)
-        cg.cp_als_iter(Yd, I, A, ALS_ITERS, lam, fit, workspace=ws)
+        cg.cp_als_iter(Yd, I, A, ALS_ITERS, lam, fit, workspace=ws, precision=prec)
 
     def barrier():
         if world > 1:
@@ -342,14 +346,14 @@ def main():
     check = {}
     if not args.no_check:
         import oracle
-        Gc = cg.cp_gradient_all(Y, I, A0, workspace=ws)
+        Gc = cg.cp_gradient_all(Y, I, A0, workspace=ws, precision=prec)
         torch.cuda.synchronize()
         want = oracle.cp_gradient_all(p.y.astype(np.float64), I, p.init)
         check["gradient_rel_err_max"] = max(
             float(np.linalg.norm(Gc[n].double().cpu().numpy() - want[n]) / np.linalg.norm(want[n]))
             for n in range(len(I)))
         Ac = [a.clone() for a in A0]
-        _, fc = cg.cp_als_iter(Y, I, Ac, 2, workspace=ws)
+        _, fc = cg.cp_als_iter(Y, I, Ac, 2, workspace=ws, precision=prec)
         tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=2)
         check["als_fit_abs_err_2sweeps"] = float(np.max(np.abs(fc.cpu().numpy() - np.array(tr.fits))))
         check["als_final_fit"] = float(fit.cpu().numpy()[-1])
@@ -360,7 +364,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "4-D FP32 tensor 100x100x100x100, rank-10 CP model (N(0,1) factors) + 20 dB noise, "
                                "R=10: one all-mode gradient + 50 fast CP_ALS sweeps per step",
-                   "I": I, "R": R, "split_k": split_point(I), "precision": "fp32", "als_iters": ALS_ITERS,
+                   "I": I, "R": R, "split_k": split_point(I), "precision": prec, "als_iters": ALS_ITERS,
                    "l2": "inputs larger than L2 (400 MB tensor)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "gradient_gflops": gradient_flops(I, R) / 1e9,
         "als_iter_per_s": None,
@@ -371,8 +375,9 @@ def main():
         "check": check,
     }
     # per-component timing outside the timed region (informational)
-    tg = _time_component(lambda: cg.cp_gradient_all(Y, I, A0, G, workspace=ws), stream)
-    ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 10, workspace=ws), stream) / 10
+    tg = _time_component(lambda: cg.cp_gradient_all(Y, I, A0, G, workspace=ws, precision=prec), stream)
+    ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 10, workspace=ws, precision=prec),
+                         stream) / 10
     line["gradient_ms"] = tg
     line["gradient_gflops"] = gradient_flops(I, R) / (tg / 1e3) / 1e9
     line["gradient_frac_of_one_pass_roofline"] = (ybytes / hbm / 1e6) / tg
