@@ -150,13 +150,17 @@ def test_gradient_full_size_sampled(cg, prec):
     Y = torch.from_numpy(p.y).cuda()
     Ad = [dev_factor(a, np.float32) for a in p.init]
     G = [g.double().cpu().numpy() for g in cg.cp_gradient_all(Y, I, Ad, precision=prec)]
+    # every entry against the oracle's explicit unfolding x Khatri-Rao product
+    want = oracle.cp_gradient_all(p.y, I, p.init)
+    for n in range(len(I)):
+        assert rel(G[n], want[n]) <= 1e-5, n
+    # and a few entries one by one from the elementwise sum (eq. 3.2)
     rng = np.random.default_rng(0)
     for n in range(len(I)):
-        for _ in range(5):
+        for _ in range(3):
             i, r = int(rng.integers(I[n])), int(rng.integers(R))
-            want = oracle.cp_gradient_entry(p.y, I, p.init, n, i, r)
-            scale = np.linalg.norm(G[n]) / np.sqrt(G[n].size)
-            assert abs(G[n][i, r] - want) <= 1e-5 * max(abs(want), scale), (n, i, r)
+            w = oracle.cp_gradient_entry(p.y, I, p.init, n, i, r)
+            assert abs(want[n][i, r] - w) <= 1e-9 * max(1.0, abs(w))
     # one ALS sweep from the same start: fit against the oracle's fit
     Ad = [dev_factor(a, np.float32) for a in p.init]
     lam, fit = cg.cp_als_iter(Y, I, Ad, 1, precision=prec)
@@ -176,7 +180,9 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     lam, fit = cg.cp_als_iter(Y, I, Ad, iters, precision=prec)
     torch.cuda.synchronize()
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=iters)
-    ftol = 1e-9 if prec == "fp64" else 1e-5
+    # Gauss-Seidel sweeps feed each gradient's error into the next factors, so
+    # the split product's ~1e-6 gradient error grows along the trajectory.
+    ftol = {"fp64": 1e-9, "fp32": 1e-5, "bf16x3": 1e-4}[prec]
     np.testing.assert_allclose(fit.cpu().numpy(), tr.fits, atol=ftol)
     if prec == "fp64":
         for n in range(len(I)):
@@ -185,12 +191,13 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     assert cg.cpg_device_status() == 0
 
 
-def test_als_one_sweep_factors_fp32(cg):
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_als_one_sweep_factors(cg, prec):
     """Per-sweep parity from identical factors."""
     I, R = [24, 20, 30, 17], 6
     p = cpsynth.make_problem(I, R, snr_db=20.0, seed=12, dtype=np.float32)
     Ad = [dev_factor(a, np.float32) for a in p.init]
-    lam, fit = cg.cp_als_iter(torch.from_numpy(p.y).cuda(), I, Ad, 1)
+    lam, fit = cg.cp_als_iter(torch.from_numpy(p.y).cuda(), I, Ad, 1, precision=prec)
     torch.cuda.synchronize()
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=1)
     for n in range(len(I)):
