@@ -65,8 +65,8 @@ int tc_rank_tile(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 
 int tc_max_nrt(int RTP, int sides, int prec) {
   const int nw = (prec == 0) ? 2 * RTP : RTP;
-  if (sides == 2) return 1 << 20;     // only the step-7 accumulator lives in tensor memory
-  return sides == 1 ? 512 / nw : 512 / nw - 1;
+  if (sides == 2) return 1 << 20;     // only the step-7 accumulators live in tensor memory
+  return sides == 1 ? 512 / nw : 512 / nw - 2;  // fused: two step-7 accumulators
 }
 
 bool tc_eligible(const float* Y, int64_t J) {

@@ -3,12 +3,13 @@
 //
 // Y is the J x K column-major matrix reshape(Y, [J_k, K_k]) (eq. 2.3); one
 // CTA owns a J-block of nrt row tiles of 128 rows and a range of columns, and
-// walks it in super-stages of (128 columns) x (one row tile):
+// walks it in super-stages of (128 columns) x (one row tile), each in its own
+// 64 KB shared buffer (NB buffers in a ring):
 //
-//   TMA      two 128 x 64 FP32 boxes per super-stage into shared memory
-//            (NBUF fp32 buffers, prefetched NBUF/2 super-stages ahead);
-//   convert  all threads split y = hi + lo (BF16 round-to-nearest each) and
-//            write hi and lo as one 128 x 128 tile of 1 KB atoms
+//   TMA      two 128 x 64 FP32 boxes fill the buffer (issued NB - 1 ahead);
+//   convert  all threads read the FP32 tile into registers, then overwrite the
+//            same buffer with y = hi + lo (BF16 round-to-nearest each), hi and
+//            lo each a 128 x 128 tile of 1 KB atoms
 //            [column group of 8][row half][8 columns][64 rows, 128-byte swizzle]
 //            which is at once the MN-major A operand of step 4 (M = rows,
 //            K = columns) and the K-major A operand of step 7 (M = columns,
@@ -21,9 +22,12 @@
 //            step 7: D_L           += A_hi [W_hi | W_lo] + A_lo W_hi
 //            (the BF16x3 split product; the plain BF16 form keeps A_hi W_hi);
 //            D_R of every row tile of the block and D_L live in tensor memory;
-//   epilogue D_L is read back (tcgen05.ld) after each column chunk's last row
-//            tile; D_R after the CTA's last column.  Outputs are the same
-//            deterministic partial sums as the CUDA-core kernel.
+//   epilogue D_L (two buffers, alternating by column chunk) is read back
+//            (tcgen05.ld) after each chunk's last row tile; D_R after the CTA's
+//            last column.  Outputs are the same deterministic partial sums as
+//            the CUDA-core kernel.
+// Converting super-stage s + 1 overlaps the MMAs of s; every buffer has its own
+// MMA-completion barrier so that no wait can miss a phase.
 //
 // Every mbarrier wait is bounded; on expiry the CTA records CPG_ERR_TIMEOUT in
 // the status word, waits (bounded) for its own operations, frees its tensor
@@ -56,22 +60,22 @@ struct TcCfg {
   static constexpr bool DO_L = (SIDES & 2) != 0;
   static constexpr bool X3 = PREC == 0;                 // BF16x3; else plain BF16
   static constexpr int NT = 256;
-  static constexpr int NBUF = (RTP >= 64) ? 2 : 4;     // fp32 128 x 64 boxes
-  static constexpr int NPAIR = NBUF / 2;
   static constexpr int NW = X3 ? 2 * RTP : RTP;         // B rows (hi, then lo)
-  static constexpr uint32_t F32_BYTES = 128 * 64 * 4;   // one TMA box
-  static constexpr uint32_t SPLIT_BYTES = 128 * 128 * 2;
+  static constexpr uint32_t BUF_BYTES = 128 * 128 * 4;  // one super-stage: fp32, then hi | lo
+  static constexpr uint32_t HALF = 128 * 64 * 4;        // one TMA box (64 columns)
   static constexpr uint32_t W_BYTES = uint32_t(NW) * 128 * 2;
-  static constexpr uint32_t OFF_F32 = 0;
-  static constexpr uint32_t OFF_HI = OFF_F32 + NBUF * F32_BYTES;
-  static constexpr uint32_t OFF_LO = OFF_HI + SPLIT_BYTES;
-  static constexpr uint32_t OFF_WR = OFF_LO + (X3 ? SPLIT_BYTES : 0);
-  static constexpr uint32_t OFF_WL = OFF_WR + (DO_R ? W_BYTES : 0);
-  static constexpr uint32_t OFF_END = OFF_WL + (DO_L ? W_BYTES : 0);
+  static constexpr int NSIDE = (DO_R ? 1 : 0) + (DO_L ? 1 : 0);
+  static constexpr uint32_t budget = 227u * 1024u - 1024u;
+  // W tiles double-buffered and three stage buffers where they fit.
+  static constexpr int WB = (2u * NSIDE * W_BYTES + 2u * BUF_BYTES <= budget) ? 2 : 1;
+  static constexpr int NB = (uint32_t(WB) * NSIDE * W_BYTES + 3u * BUF_BYTES <= budget) ? 3 : 2;
+  static constexpr uint32_t OFF_BUF = 0;
+  static constexpr uint32_t OFF_WR = OFF_BUF + NB * BUF_BYTES;
+  static constexpr uint32_t OFF_WL = OFF_WR + (DO_R ? WB * W_BYTES : 0);
+  static constexpr uint32_t OFF_END = OFF_WL + (DO_L ? WB * W_BYTES : 0);
   static constexpr size_t smem_bytes = OFF_END + 1024;  // + alignment slack
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
   static_assert(RTP % 16 == 0 && RTP <= 64, "MMA N must be a multiple of 16");
-  static constexpr int max_nrt = DO_R && DO_L ? (512 / (2 * RTP)) - 1 : 1;
 };
 
 // Byte offset of element (row j, column c) of the split tile.
@@ -111,8 +115,8 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   constexpr int NT = C::NT;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t bar_full[C::NBUF];
-  __shared__ uint64_t bar_mma;
+  __shared__ uint64_t bar_full[C::NB];
+  __shared__ uint64_t bar_mma[C::NB];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
 
@@ -126,14 +130,16 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   const int64_t kend = (kbeg + a.Kc < K) ? (kbeg + a.Kc) : K;
   const int nchunk = int((kend - kbeg + 127) / 128);
   const int nss = nchunk * nrt;
-  const int tcols_needed = (DO_R ? nrt : 0) * C::NW + (DO_L ? C::NW : 0);
+  const int tcols_needed = (DO_R ? nrt : 0) * C::NW + (DO_L ? 2 * C::NW : 0);
   uint32_t tcols = 32;
   while (tcols < uint32_t(tcols_needed)) tcols <<= 1;
-  const uint32_t colL = (DO_R ? nrt : 0) * C::NW;
+  const uint32_t colL0 = (DO_R ? nrt : 0) * C::NW;
 
   if (tid == 0) {
-    for (int b = 0; b < C::NBUF; ++b) tc::mbar_init(&bar_full[b], 1);
-    tc::mbar_init(&bar_mma, 1);
+    for (int b = 0; b < C::NB; ++b) {
+      tc::mbar_init(&bar_full[b], 1);
+      tc::mbar_init(&bar_mma[b], 1);
+    }
     tc::mbar_fence_init();
     abort_flag = 0;
   }
@@ -147,17 +153,16 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   int mma_issued = 0;   // super-stages whose MMAs thread 0 has issued
   auto issue_tma = [&](int ss) {  // thread 0 only
     last_issued = ss + 1;
-    const int pair = ss % C::NPAIR;
+    const int b = ss % C::NB;
     const int64_t cb = kbeg + int64_t(ss / nrt) * 128;
     const int64_t j0 = jblk + int64_t(ss % nrt) * 128;
-    for (int h = 0; h < 2; ++h) {
-      uint64_t* bar = &bar_full[2 * pair + h];
-      tc::mbar_arrive_expect_tx(bar, C::F32_BYTES);
-      tc::tma_load_2d(sm + C::OFF_F32 + (2 * pair + h) * C::F32_BYTES, &tmap, int(j0), int(cb + 64 * h), bar);
-    }
+    uint64_t* bar = &bar_full[b];
+    tc::mbar_arrive_expect_tx(bar, C::BUF_BYTES);
+    for (int h = 0; h < 2; ++h)
+      tc::tma_load_2d(sm + C::OFF_BUF + b * C::BUF_BYTES + h * C::HALF, &tmap, int(j0), int(cb + 64 * h), bar);
   };
   if (tid == 0) {
-    for (int ss = 0; ss < C::NPAIR && ss < nss; ++ss) issue_tma(ss);
+    for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue_tma(ss);
   }
 
   // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).
@@ -180,12 +185,13 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   // L epilogue: D_L rows are the chunk's 128 columns.
   auto epilogue_L = [&](int q) {
     if (warp < 4) {
+      const uint32_t col = colL0 + uint32_t(q & 1) * C::NW;
       const int64_t c = kbeg + int64_t(q) * 128 + 32 * warp + lane;
       float v[16], u[16];
 #pragma unroll
       for (int r16 = 0; r16 < RTP; r16 += 16) {
-        tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + colL + r16, v);
-        if constexpr (X3) tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + colL + RTP + r16, u);
+        tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + col + r16, v);
+        if constexpr (X3) tc::tmem_ld16(tbase + (uint32_t(32 * warp) << 16) + col + RTP + r16, u);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int r = r0 + r16 + i;
@@ -200,74 +206,76 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   float ysq = 0.f;  // this thread's share of sum y^2 (rows beyond J are zero)
   bool ok = true;
   for (int ss = 0; ss < nss; ++ss) {
-    const int q = ss / nrt, rt = ss % nrt, pair = ss % C::NPAIR;
-    const uint32_t par = uint32_t(ss / C::NPAIR) & 1u;
-    if (!tc::mbar_wait(&bar_full[2 * pair], par) || !tc::mbar_wait(&bar_full[2 * pair + 1], par)) ok = false;
-    if (ss > 0 && !tc::mbar_wait(&bar_mma, uint32_t(ss - 1) & 1u)) ok = false;
-    if (!ok) {
-      atomicExch(&abort_flag, 1);
+    const int q = ss / nrt, rt = ss % nrt, b = ss % C::NB;
+    if (!tc::mbar_wait(&bar_full[b], uint32_t(ss / C::NB) & 1u)) ok = false;
+    if (C::WB == 1 && ss > 0) {  // single W tiles: MMA(ss - 1) must be done before they are rewritten
+      if (!tc::mbar_wait(&bar_mma[(ss - 1) % C::NB], uint32_t((ss - 1) / C::NB) & 1u)) ok = false;
     }
-    tc::tc_fence_after();
-    __syncthreads();
+    if (!ok) atomicExch(&abort_flag, 1);
+    unsigned char* buf = sm + C::OFF_BUF + b * C::BUF_BYTES;
+    // 1. FP32 tile -> registers (two half-chunk reads ordered to avoid bank conflicts).
+    const int64_t cb = kbeg + int64_t(q) * 128;
+    float x[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int task = tid + NT * u;
+      const int c = task >> 4, jq = task & 15;
+      const int first = (jq >> 2) & 1;
+      const float* src = reinterpret_cast<const float*>(buf + (c >> 6) * C::HALF + (c & 63) * 512 + jq * 32);
+      const float4 pa = reinterpret_cast<const float4*>(src)[first];
+      const float4 pb = reinterpret_cast<const float4*>(src)[first ^ 1];
+      const float4 p0 = first ? pb : pa, p1 = first ? pa : pb;
+      x[u][0] = p0.x; x[u][1] = p0.y; x[u][2] = p0.z; x[u][3] = p0.w;
+      x[u][4] = p1.x; x[u][5] = p1.y; x[u][6] = p1.z; x[u][7] = p1.w;
+      if constexpr (DO_R) {
+        if (do_norm && cb + c < kend) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) ysq = fmaf(x[u][e], x[u][e], ysq);
+        }
+      }
+    }
+    __syncthreads();  // the whole FP32 tile is in registers; abort_flag is settled
     if (abort_flag) {
       ok = false;
       break;
     }
-    if constexpr (DO_L) {
-      if (ss > 0 && (ss - 1) % nrt == nrt - 1) epilogue_L(q - 1);
-    }
-    // Split the two fp32 boxes into the BF16 hi / lo tile.
-    {
-      const int64_t cb0 = kbeg + int64_t(q) * 128;
-      const unsigned char* f32 = sm + C::OFF_F32 + (2 * pair) * C::F32_BYTES;
-      for (int task = tid; task < 128 * 16; task += NT) {
-        const int c = task >> 4, jq = task & 15;
-        const float* src = reinterpret_cast<const float*>(f32 + (c >> 6) * C::F32_BYTES + (c & 63) * 512 + jq * 32);
-        const float4 p0 = reinterpret_cast<const float4*>(src)[0];
-        const float4 p1 = reinterpret_cast<const float4*>(src)[1];
-        const float x[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-        if constexpr (DO_R) {
-          if (do_norm && cb0 + c < kend) {
+    // 2. Overwrite the buffer with the BF16 hi | lo split tile.
 #pragma unroll
-            for (int e = 0; e < 8; ++e) ysq = fmaf(x[e], x[e], ysq);
-          }
-        }
-        uint4 hi, lo;
-        split8(x, hi, lo);
-        const uint32_t off = split_off(jq * 8, c);
-        *reinterpret_cast<uint4*>(sm + C::OFF_HI + off) = hi;
-        if constexpr (X3) *reinterpret_cast<uint4*>(sm + C::OFF_LO + off) = lo;
-      }
+    for (int u = 0; u < 8; ++u) {
+      const int task = tid + NT * u;
+      const int c = task >> 4, jq = task & 15;
+      uint4 hi, lo;
+      split8(x[u], hi, lo);
+      const uint32_t off = split_off(jq * 8, c);
+      *reinterpret_cast<uint4*>(buf + off) = hi;
+      if constexpr (X3) *reinterpret_cast<uint4*>(buf + 128 * 128 * 2 + off) = lo;
     }
-    const int64_t cb = kbeg + int64_t(q) * 128;
+    // 3. Khatri-Rao tiles of this super-stage.
     const int64_t j0 = jblk + int64_t(rt) * 128;
-    if constexpr (DO_R) {
-      if (rt == 0) gen_w(sm + C::OFF_WR, a.wr, cb, kend);
-    }
-    if constexpr (DO_L) {
-      if (nrt > 1 || ss == 0) gen_w(sm + C::OFF_WL, a.wl, j0, J);
-    }
+    const int wb = ss % C::WB;
+    if constexpr (DO_R) gen_w(sm + C::OFF_WR + wb * C::W_BYTES, a.wr, cb, kend);
+    if constexpr (DO_L) gen_w(sm + C::OFF_WL + wb * C::W_BYTES, a.wl, j0, J);
     tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
+    // 4. MMAs of this super-stage.
     if (tid == 0) {
       tc::tc_fence_after();
-      if (ss + C::NPAIR < nss) issue_tma(ss + C::NPAIR);
-      const uint32_t hi0 = tc::smem_addr(sm + C::OFF_HI), lo0 = tc::smem_addr(sm + C::OFF_LO);
+      const uint32_t hi0 = tc::smem_addr(buf), lo0 = hi0 + 128 * 128 * 2;
       if constexpr (DO_R) {
-        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR);
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR + wb * C::W_BYTES);
         const uint32_t d = tbase + uint32_t(rt) * C::NW;
         for (int s = 0; s < 8; ++s) {
           const uint64_t bd = tc::smem_desc_sw128(w0 + (s >> 2) * 1024 + (s & 3) * 32, 16, 2048);
-          tc::mma_bf16(d, tc::smem_desc_sw128(hi0 + s * 4096, 1024, 2048), bd,
-                       tc::idesc_bf16_f32(128, C::NW, 1, 0), (q > 0 || s > 0) ? 1u : 0u);
+          tc::mma_bf16(d, tc::smem_desc_sw128(hi0 + s * 4096, 1024, 2048), bd, tc::idesc_bf16_f32(128, C::NW, 1, 0),
+                       (q > 0 || s > 0) ? 1u : 0u);
           if constexpr (X3)
             tc::mma_bf16(d, tc::smem_desc_sw128(lo0 + s * 4096, 1024, 2048), bd, tc::idesc_bf16_f32(128, RTP, 1, 0), 1u);
         }
       }
       if constexpr (DO_L) {
-        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL);
-        const uint32_t d = tbase + colL;
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + wb * C::W_BYTES);
+        const uint32_t d = tbase + colL0 + uint32_t(q & 1) * C::NW;
         for (int s = 0; s < 8; ++s) {
           const uint32_t koff = (s >> 2) * 1024 + (s & 3) * 32;
           const uint64_t bd = tc::smem_desc_sw128(w0 + koff, 16, 2048);
@@ -277,15 +285,26 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
             tc::mma_bf16(d, tc::smem_desc_sw128(lo0 + koff, 16, 2048), bd, tc::idesc_bf16_f32(128, RTP, 0, 0), 1u);
         }
       }
-      tc::mma_commit(&bar_mma);
+      tc::mma_commit(&bar_mma[b]);
       mma_issued = ss + 1;
+    }
+    // 5. Retire super-stage ss - 1: its MMAs are done, so its chunk's D_L can be
+    //    read and its buffer refilled.
+    if (ss > 0) {
+      const int p = ss - 1;
+      if (!tc::mbar_wait(&bar_mma[p % C::NB], uint32_t(p / C::NB) & 1u)) atomicExch(&abort_flag, 1);
+      tc::tc_fence_after();
+      if constexpr (DO_L) {
+        if (p % nrt == nrt - 1 && !abort_flag) epilogue_L(p / nrt);
+      }
+      if (tid == 0 && p + C::NB < nss && !abort_flag) issue_tma(p + C::NB);
     }
   }
 
   __syncthreads();  // every thread has left the loop
   bool aborted = abort_flag != 0;
   if (!aborted && nss > 0) {
-    if (!tc::mbar_wait(&bar_mma, uint32_t(nss - 1) & 1u)) atomicExch(&abort_flag, 1);
+    if (!tc::mbar_wait(&bar_mma[(nss - 1) % C::NB], uint32_t((nss - 1) / C::NB) & 1u)) atomicExch(&abort_flag, 1);
     tc::tc_fence_after();
     __syncthreads();
     aborted = abort_flag != 0;
@@ -330,13 +349,11 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   if (aborted && tid == 0) {
     atomicCAS(a.status, 0, int(CPG_ERR_TIMEOUT));
     // Let this CTA's own copies and MMAs drain (bounded) before its memory is released.
-    for (int ss = 0; ss < last_issued; ++ss) {
-      const int pair = ss % C::NPAIR;
-      const uint32_t par = uint32_t(ss / C::NPAIR) & 1u;
-      tc::mbar_wait(&bar_full[2 * pair], par, 1u << 16);
-      tc::mbar_wait(&bar_full[2 * pair + 1], par, 1u << 16);
-    }
-    tc::mbar_wait(&bar_mma, uint32_t(mma_issued - 1) & 1u, 1u << 20);
+    // Newest phase of every buffer's barriers only (older phases have completed).
+    for (int ss = (last_issued > C::NB ? last_issued - C::NB : 0); ss < last_issued; ++ss)
+      tc::mbar_wait(&bar_full[ss % C::NB], uint32_t(ss / C::NB) & 1u, 1u << 16);
+    for (int ss = (mma_issued > C::NB ? mma_issued - C::NB : 0); ss < mma_issued; ++ss)
+      tc::mbar_wait(&bar_mma[ss % C::NB], uint32_t(ss / C::NB) & 1u, 1u << 16);
   }
   tc::tc_fence_before();
   __syncthreads();
