@@ -202,7 +202,8 @@ def test_als_one_sweep_factors(cg, prec):
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=1)
     for n in range(len(I)):
         assert rel(Ad[n].double().cpu().numpy(), tr.A[n]) <= 1e-5, n
-    np.testing.assert_allclose(lam.cpu().numpy(), tr.lam, rtol=1e-5)
+    # lambda is the norm of G V^{-1}: the solve amplifies the split product's error
+    np.testing.assert_allclose(lam.cpu().numpy(), tr.lam, rtol={"fp32": 1e-5, "bf16x3": 5e-5}[prec])
 
 
 def test_als_noiseless_fit_to_one(cg):
