@@ -165,20 +165,19 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
     for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue_tma(ss);
   }
 
-  // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).
+  // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).  Lanes
+  // take consecutive index pairs of one rank, so factor loads coalesce and
+  // every lane stores one packed BF16 pair per row.
   auto gen_w = [&](unsigned char* tile, const KrRows<float>& kr, int64_t base, int64_t limit) {
-    for (int task = tid; task < RTP * 16; task += NT) {
-      const int n = task >> 4, kq = task & 15;
-      float w[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int64_t g = base + kq * 8 + e;
-        w[e] = (g < limit && r0 + n < R) ? kr.at(uint32_t(g), r0 + n) : 0.f;
-      }
-      uint4 hi, lo;
-      split8(w, hi, lo);
-      *reinterpret_cast<uint4*>(tile + wtile_off(n, kq * 8)) = hi;
-      if constexpr (X3) *reinterpret_cast<uint4*>(tile + wtile_off(RTP + n, kq * 8)) = lo;
+    for (int task = tid; task < RTP * 64; task += NT) {
+      const int n = task >> 6, kp = task & 63;
+      const int64_t g = base + 2 * kp;
+      const bool rok = r0 + n < R;
+      const float w0 = (rok && g < limit) ? kr.at(uint32_t(g), r0 + n) : 0.f;
+      const float w1 = (rok && g + 1 < limit) ? kr.at(uint32_t(g + 1), r0 + n) : 0.f;
+      const float h0 = __bfloat162float(__float2bfloat16_rn(w0)), h1 = __bfloat162float(__float2bfloat16_rn(w1));
+      *reinterpret_cast<uint32_t*>(tile + wtile_off(n, 2 * kp)) = pack_bf16(h0, h1);
+      if constexpr (X3) *reinterpret_cast<uint32_t*>(tile + wtile_off(RTP + n, 2 * kp)) = pack_bf16(w0 - h0, w1 - h1);
     }
   };
 
@@ -252,9 +251,16 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
     }
     // 3. Khatri-Rao tiles of this super-stage.
     const int64_t j0 = jblk + int64_t(rt) * 128;
-    const int wb = ss % C::WB;
-    if constexpr (DO_R) gen_w(sm + C::OFF_WR + wb * C::W_BYTES, a.wr, cb, kend);
-    if constexpr (DO_L) gen_w(sm + C::OFF_WL + wb * C::W_BYTES, a.wl, j0, J);
+    // W_R depends on the column chunk only (buffer q % WB, rebuilt at its first
+    // row tile); W_L on the row tile (buffer ss % WB).  The buffer being
+    // rebuilt was last read by MMAs that have completed.
+    const int wbr = q % C::WB, wbl = ss % C::WB;
+    if constexpr (DO_R) {
+      if (rt == 0) gen_w(sm + C::OFF_WR + wbr * C::W_BYTES, a.wr, cb, kend);
+    }
+    if constexpr (DO_L) {
+      if (nrt > 1 || ss == 0 || C::WB == 1) gen_w(sm + C::OFF_WL + wbl * C::W_BYTES, a.wl, j0, J);
+    }
     tc::fence_async_smem();
     tc::tc_fence_before();
     __syncthreads();
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
       tc::tc_fence_after();
       const uint32_t hi0 = tc::smem_addr(buf), lo0 = hi0 + 128 * 128 * 2;
       if constexpr (DO_R) {
-        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR + wb * C::W_BYTES);
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR + wbr * C::W_BYTES);
         const uint32_t d = tbase + uint32_t(rt) * C::NW;
         for (int s = 0; s < 8; ++s) {
           const uint64_t bd = tc::smem_desc_sw128(w0 + (s >> 2) * 1024 + (s & 3) * 32, 16, 2048);
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
         }
       }
       if constexpr (DO_L) {
-        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + wb * C::W_BYTES);
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + (nrt > 1 || C::WB == 1 ? wbl : 0) * C::W_BYTES);
         const uint32_t d = tbase + colL0 + uint32_t(q & 1) * C::NW;
         for (int s = 0; s < 8; ++s) {
           const uint32_t koff = (s >> 2) * 1024 + (s & 3) * 32;
