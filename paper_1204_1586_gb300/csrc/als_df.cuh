@@ -66,7 +66,7 @@ constexpr int kAlsThreads = 1024;
 // One block of kAlsThreads threads.  Shared memory: als_df_smem_bytes(In, R).
 // Phases (each a short dependent chain, all rows / columns in parallel):
 //   Cholesky    right-looking, pivots from a reciprocal square root (no divide)
-//   L^{-1}      column c by R rank-1 steps (lane c owns its column)
+//   L^{-1}      R elimination steps, lanes over the entries of a step
 //   V^{-1}      = L^{-T} L^{-1}, one output per thread
 //   X           = G V^{-1}, one output per thread
 //   lambda      warp per column; Gram: 8 lanes per (p, q) pair.
@@ -156,12 +156,32 @@ __global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfA
     return;
   }
 
-  // L^{-1}: thread c owns column c; step j finalises row j and eliminates it below.
-  for (int c = tid; c < R; c += nt) {
-    for (int j = c; j < R; ++j) {
-      const df t = df_mul(Li[j + R * c], dinv[j]);
-      Li[j + R * c] = t;
-      for (int i = j + 1; i < R; ++i) Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], t));
+  // L^{-1} by R elimination steps (L x = e_c for every column c at once): step
+  // j finalises row j of L^{-1} and removes it from the rows below.  Warp 0
+  // for R <= 32 (lanes over the (row, column) entries of a step), else the block.
+  if (R <= 32) {
+    if (warp == 0) {
+      for (int j = 0; j < R; ++j) {
+        for (int c = lane; c <= j; c += 32) Li[j + R * c] = df_mul(Li[j + R * c], dinv[j]);
+        __syncwarp();
+        const int rows = R - 1 - j, cols = j + 1;
+        for (int e = lane; e < rows * cols; e += 32) {
+          const int i = j + 1 + e % rows, c = e / rows;
+          Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], Li[j + R * c]));
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    for (int j = 0; j < R; ++j) {
+      for (int c = tid; c <= j; c += nt) Li[j + R * c] = df_mul(Li[j + R * c], dinv[j]);
+      __syncthreads();
+      const int rows = R - 1 - j, cols = j + 1;
+      for (int e = tid; e < rows * cols; e += nt) {
+        const int i = j + 1 + e % rows, c = e / rows;
+        Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], Li[j + R * c]));
+      }
+      __syncthreads();
     }
   }
   __syncthreads();

@@ -80,13 +80,14 @@ __device__ __forceinline__ df df_sqrt(df a) {
   return quick_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
 }
 
-// 1 / sqrt(a) for a > 0: FP32 reciprocal-sqrt seed, then one Newton step
-// y <- y + y (1 - a y^2) / 2 carried in double-float (doubles the 24 seed bits).
+// 1 / sqrt(a) for a > 0: FP32 reciprocal-sqrt seed y0, then one Newton step
+// y = y0 + y0 (1 - a y0^2) / 2.  The residual e = 1 - a y0^2 is formed in
+// double-float (y0^2 exactly by TwoProd); the small correction y0 e / 2 needs
+// only float precision, so the result carries about twice the seed's bits.
 __device__ __forceinline__ df df_rsqrt(df a) {
   const float y0 = rsqrtf(a.hi);
-  const df y = df_make(y0);
-  const df e = df_sub(df_make(1.f), df_mul(a, df_mul(y, y)));  // 1 - a y^2
-  return df_add(y, df_mul_f(df_mul(y, e), 0.5f));
+  const df e = df_sub(df_make(1.f), df_mul(a, two_prod(y0, y0)));
+  return quick_two_sum(y0, __fmul_rn(__fmul_rn(y0, e.hi), 0.5f));
 }
 
 __device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }

@@ -96,16 +96,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// hi = bf16(x), lo = bf16(x - hi) for 8 values; packed 16 bytes each.
+// hi = bf16(x), lo = bf16(x - hi) (round-to-nearest each) for a pair, with
+// one paired conversion per limb; hi is unpacked exactly to form x - hi.
+__device__ __forceinline__ uint32_t split2(float x0, float x1, uint32_t& lo) {
+  const uint32_t hp = pack_bf16(x0, x1);
+  const float h0 = __uint_as_float(hp << 16), h1 = __uint_as_float(hp & 0xffff0000u);
+  lo = pack_bf16(x0 - h0, x1 - h1);
+  return hp;
+}
+// The same for 8 values; packed 16 bytes each.
 __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
-  float h[8], l[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    h[e] = __bfloat162float(__float2bfloat16_rn(x[e]));
-    l[e] = x[e] - h[e];
-  }
-  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+  hi.x = split2(x[0], x[1], lo.x);
+  hi.y = split2(x[2], x[3], lo.y);
+  hi.z = split2(x[4], x[5], lo.z);
+  hi.w = split2(x[6], x[7], lo.w);
 }
 
 template <int RTP, int SIDES, int PREC>
