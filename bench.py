@@ -86,6 +86,29 @@ def step_flops(I, R, iters):
     return gradient_flops(I, R) + iters * als_sweep_flops(I, R)
 
 
+# ---- ranks (replicas: each rank decomposes its own tensor, no data-path collective) ----
+def rank_seed(rank):
+    """Seed of the tensor that rank `rank` decomposes (independent problems)."""
+    return cpsynth.DEFAULT_SEED + int(rank)
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of `values` over all ranks of the initialised
+    process group (the job takes as long as its slowest rank); the values
+    themselves when there is no group or a single rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_value(flops_per_rank_step, world, ms):
+    """Whole-job GFLOP/s: every rank's step flops over the slowest rank's step time."""
+    return world * flops_per_rank_step / (ms / 1e3) / 1e9
+
+
 # ---- clocks ---------------------------------------------------------------------------
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -235,7 +258,7 @@ def main():
     cg.lib()
 
     # Each rank decomposes its own tensor (independent problems: weak scaling, no data-path collective).
-    p = cpsynth.workload(WORKLOAD, seed=cpsynth.DEFAULT_SEED + rank)
+    p = cpsynth.workload(WORKLOAD, seed=rank_seed(rank))
     I, R = p.I, p.R
     Y = torch.from_numpy(p.y).to(dev)
     A0 = [cg.colmajor(torch.from_numpy(a.astype(np.float32)).to(dev)) for a in p.init]
@@ -315,14 +338,11 @@ def main():
     h2d = Yh.numel() * 4 + sum(a.numel() * 4 for a in Ad_h)
     d2h = sum(h.numel() * 4 for h in out_h) + fit_h.numel() * 8
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
 
     flops = step_flops(I, R, ALS_ITERS)
-    value = world * flops / (ms / 1e3) / 1e9
-    value_e2e = world * flops / (ms_e2e / 1e3) / 1e9
+    value = job_value(flops, world, ms)
+    value_e2e = job_value(flops, world, ms_e2e)
 
     if rank != 0:
         if world > 1:
@@ -337,9 +357,11 @@ def main():
         per_side.setdefault({1: "step4_R", 2: "step7_L", 3: "step4+7_fused"}[s], []).append(t)
     avg = sum(lead_ms) / len(lead_ms) if lead_ms else float("nan")
     achieved = ybytes / (avg / 1e3) / 1e9
-    traffic = lead_traffic()
+    # The split-BF16 forms run the tensor-core kernel (J = 10^4 rows are whole 16-byte chunks).
+    kernel = "lead_simt_kernel" if prec == "fp32" else "lead_tc_kernel"
+    traffic = lead_traffic(kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "lead_simt_kernel (Algorithm 2 steps 4/7)",
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": f"{kernel} (Algorithm 2 steps 4/7)",
                 "launches": len(lead_ms),
                 "per_variant_GBps": {k: ybytes / (sum(v) / len(v) / 1e3) / 1e9 for k, v in per_side.items()}}
 
@@ -391,22 +413,30 @@ def main():
     return 0
 
 
-def lead_kernel_hash():
+LEAD_KERNELS = {
+    # kernel family -> (sources whose hash identifies the captured build, traffic summary)
+    "lead_simt_kernel": (("lead_simt.cuh", "common.cuh"), "lead_simt_traffic.json"),
+    "lead_tc_kernel": (("lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tc_traffic.json"),
+}
+
+
+def lead_kernel_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in ("lead_simt.cuh", "common.cuh"):
+    for f in LEAD_KERNELS[kernel][0]:
         with open(os.path.join(ROOT, "paper_1204_1586_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def lead_traffic():
+def lead_traffic(kernel):
     """DRAM bytes per launch of the leading kernel from the committed ncu
     summary, or None when the kernel source changed since it was captured."""
-    tf = os.path.join(ROOT, "profiles", "lead_traffic.json")
+    tf = os.path.join(ROOT, "profiles", LEAD_KERNELS[kernel][1])
     try:
-        d = json.load(open(tf))
-        if d.get("kernel_source_hash") == lead_kernel_hash():
+        with open(tf) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") == lead_kernel_hash(kernel):
             return d.get("bytes_per_launch")
     except Exception:
         pass
