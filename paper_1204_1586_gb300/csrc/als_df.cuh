@@ -3,19 +3,25 @@
 //
 // For mode n, with the gradient G = Y_(n) KR from the chain kernels:
 //   V        = Hadamard_{m != n} Gram_m          (Gram_m = A^(m)T A^(m))
-//   V        = L L^T                             (Cholesky)
-//   X        = G V^{-1}                          (V^{-1} = L^{-T} L^{-1})
+//   V^{-1}   by Gauss-Jordan elimination of [V | I]
+//   X        = G V^{-1}
 //   lambda_q = ||x_q||,  a_q = x_q / lambda_q    (column normalisation)
 //   Gram_n   = A^(n)T A^(n) of the stored FP32 factor (products exact, sums compensated)
 // and after the last mode of a sweep the fit from R x R quantities:
 //   <Y, Yhat> = sum_q lambda_q a_q^T g_q,  ||Yhat||^2 = lambda^T (Hadamard_m Gram_m) lambda,
 //   fit = 1 - sqrt(max(0, ||Y||^2 - 2 <Y,Yhat> + ||Yhat||^2)) / ||Y||.
+// V is symmetric positive definite whenever the Grams are (a Hadamard product
+// of positive definite matrices is positive definite, Schur product theorem),
+// so the elimination needs no pivoting and its pivots are the positive Schur
+// complements that a Cholesky factorisation would take square roots of; a
+// pivot that is not positive marks V as not positive definite, and then
+// A^(n), lambda and Gram_n are left untouched and CPG_ERR_SINGULAR is
+// recorded in the device status word.
 // Every quantity of the normal equations is a double-float (about 48-bit
 // significand) so that their conditioning is handled at FP64-like accuracy on
 // the FP32 pipe; the measured FP64 rate of this GPU (64-cycle dependent FMA,
 // ~680-cycle divide) would put tens of microseconds on the critical path of
-// every update.  A V whose pivot is not positive leaves A^(n), lambda and
-// Gram_n untouched and records CPG_ERR_SINGULAR in the device status word.
+// every update.
 #pragma once
 
 #include "chain.cuh"
@@ -49,10 +55,15 @@ __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
   grams[(int64_t(m) * R + b) * R + a] = s;
 }
 
+// Threads of the update block: enough for one Gauss-Jordan entry and about two
+// entries of X per thread at small ranks.
+inline int als_df_threads(int R) { return R <= 16 ? 512 : 1024; }
+
 inline size_t als_df_smem_bytes(int64_t In, int R) {
   const size_t RS = size_t(R) + 1;
-  return 3 * size_t(R) * R * sizeof(df) + 4 * size_t(R) * sizeof(df) + size_t(In) * RS * (sizeof(df) + sizeof(float)) +
-         16;
+  // [V | I] (R x 2R), two column and two row buffers, lambda, 1/lambda, partials, X, the factor panel.
+  return (2 * size_t(R) * R + 2 * size_t(R) + 4 * size_t(R) + 3 * size_t(R)) * sizeof(df) +
+         size_t(In) * RS * (sizeof(df) + sizeof(float)) + 16;
 }
 
 __device__ __forceinline__ df df_warp_sum(df v) {
@@ -61,29 +72,26 @@ __device__ __forceinline__ df df_warp_sum(df v) {
   return v;
 }
 
-constexpr int kAlsThreads = 1024;
-
-// One block of kAlsThreads threads.  Shared memory: als_df_smem_bytes(In, R).
-// Phases (each a short dependent chain, all rows / columns in parallel):
-//   Cholesky    right-looking, pivots from a reciprocal square root (no divide)
-//   L^{-1}      R elimination steps, lanes over the entries of a step
-//   V^{-1}      = L^{-T} L^{-1}, one output per thread
-//   X           = G V^{-1}, one output per thread
-//   lambda      warp per column; Gram: 8 lanes per (p, q) pair.
-__global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfArgs a) {
+// One block of als_df_threads(R) threads.  Shared memory: als_df_smem_bytes(In, R).
+// Phases (each a short dependent chain, all entries in parallel):
+//   V^{-1}   R Gauss-Jordan steps on [V | I], one barrier each: step j
+//            scales row j by 1 / pivot and removes column j from the other
+//            rows, reading row j and column j from the side buffers written
+//            by step j - 1 (so every entry updates in place);
+//   X        = G V^{-1}, one output per thread;
+//   lambda   warp per column; Gram: 8 lanes per (p, q) pair.
+__global__ void __launch_bounds__(1024) als_update_df_kernel(const AlsDfArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int R = a.R, N = a.N, n = a.n, RS = R + 1;
+  const int R = a.R, N = a.N, n = a.n, RS = R + 1, R2 = 2 * R;
   const int64_t In = a.In;
-  df* V = reinterpret_cast<df*>(smraw);      // V, then L (lower, V[i + R*j])
-  df* Li = V + R * R;                        // L^{-1} (lower, Li[i + R*c])
-  df* Vi = Li + R * R;                       // V^{-1}
-  df* dinv = Vi + R * R;                     // 1 / L[j][j]
-  df* lam = dinv + R;                        // lambda_q
+  df* M = reinterpret_cast<df*>(smraw);      // [V | I], row-major: M[i * 2R + c]
+  df* colb = M + R * R2;                     // column j of M, two buffers of R
+  df* rowb = colb + 2 * R;                   // row j of M, two buffers of 2R
+  df* lam = rowb + 2 * R2;                   // lambda_q
   df* ilam = lam + R;                        // 1 / lambda_q
   df* part = ilam + R;                       // per-column partial inner products
   df* X = part + R;                          // X[i*RS + q]
   float* Af = reinterpret_cast<float*>(X + In * RS);  // G, then the stored factor: Af[i*RS + q]
-  __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
   for (int64_t t = tid; t < In * R; t += nt) {
@@ -91,125 +99,64 @@ __global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfA
     const int64_t i = t - int64_t(q) * In;
     Af[i * RS + q] = a.G[t];
   }
-  for (int t = tid; t < R * R; t += nt) {
-    df v{1.f, 0.f};
-    for (int m = 0; m < N; ++m)
-      if (m != n) v = df_mul(v, a.grams[int64_t(m) * R * R + t]);
-    V[t] = v;
-    const int i = t % R, c = t / R;
-    Li[t] = df_make(i == c ? 1.f : 0.f);
+  for (int e = tid; e < R * R2; e += nt) {
+    const int i = e / R2, c = e - i * R2;
+    df v;
+    if (c < R) {
+      v = df_make(1.f);
+      for (int m = 0; m < N; ++m)
+        if (m != n) v = df_mul(v, a.grams[int64_t(m) * R * R + i + R * c]);
+    } else {
+      v = df_make(c - R == i ? 1.f : 0.f);
+    }
+    M[e] = v;
+    if (c == 0) colb[i] = v;
+    if (i == 0) rowb[c] = v;
   }
-  if (tid == 0) fail = 0;
   __syncthreads();
 
-  // Right-looking Cholesky V = L L^T; sqrt(d) = d * rsqrt(d), 1/L[j][j] = rsqrt(d).
-  if (R <= 32) {
-    if (warp == 0) {
-      for (int j = 0; j < R; ++j) {
-        const df d = V[j + R * j];
-        if (!(d.hi > 0.f)) {
-          if (lane == 0) fail = 1;
-          break;
-        }
-        const df rs = df_rsqrt(d);
-        __syncwarp();
-        if (lane == j) {
-          V[j + R * j] = df_mul(d, rs);
-          dinv[j] = rs;
-        }
-        if (lane > j && lane < R) V[lane + R * j] = df_mul(V[lane + R * j], rs);
-        __syncwarp();
-        const int m = R - 1 - j;
-        for (int e = lane; e < m * m; e += 32) {
-          const int ii = j + 1 + e % m, ll = j + 1 + e / m;
-          if (ll <= ii) V[ii + R * ll] = df_sub(V[ii + R * ll], df_mul(V[ii + R * j], V[ll + R * j]));
-        }
-        __syncwarp();
-      }
+  // Gauss-Jordan: after step j, columns <= j of the left half are unit
+  // vectors (never read again) and the right half holds the running inverse.
+  bool fail = false;
+  for (int j = 0; j < R; ++j) {
+    const df* col = colb + (j & 1) * R;
+    const df* row = rowb + (j & 1) * R2;
+    df* coln = colb + ((j + 1) & 1) * R;
+    df* rown = rowb + ((j + 1) & 1) * R2;
+    const df p = col[j];
+    if (!(p.hi > 0.f)) {  // every thread read the same pivot
+      fail = true;
+      break;
     }
-  } else {
-    for (int j = 0; j < R; ++j) {
-      const df d = V[j + R * j];
-      if (!(d.hi > 0.f)) {
-        if (tid == 0) fail = 1;
-        break;  // every thread read the same d
-      }
-      const df rs = df_rsqrt(d);
-      __syncthreads();
-      if (tid == j) {
-        V[j + R * j] = df_mul(d, rs);
-        dinv[j] = rs;
-      }
-      for (int i = j + 1 + tid; i < R; i += nt) V[i + R * j] = df_mul(V[i + R * j], rs);
-      __syncthreads();
-      const int m = R - 1 - j;
-      for (int e = tid; e < m * m; e += nt) {
-        const int ii = j + 1 + e % m, ll = j + 1 + e / m;
-        if (ll <= ii) V[ii + R * ll] = df_sub(V[ii + R * ll], df_mul(V[ii + R * j], V[ll + R * j]));
-      }
-      __syncthreads();
+    const df inv = df_rcp(p);
+    for (int e = tid; e < R * R2; e += nt) {
+      const int i = e / R2, c = e - i * R2;
+      if (c <= j) continue;
+      const df v = (i == j) ? df_mul(row[c], inv) : df_sub(M[e], df_mul(df_mul(col[i], inv), row[c]));
+      M[e] = v;
+      if (c == j + 1) coln[i] = v;
+      if (i == j + 1) rown[c] = v;
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (fail) {
     if (tid == 0) atomicCAS(a.status, 0, int(CPG_ERR_SINGULAR));
     return;
   }
 
-  // L^{-1} by R elimination steps (L x = e_c for every column c at once): step
-  // j finalises row j of L^{-1} and removes it from the rows below.  Warp 0
-  // for R <= 32 (lanes over the (row, column) entries of a step), else the block.
-  if (R <= 32) {
-    if (warp == 0) {
-      for (int j = 0; j < R; ++j) {
-        for (int c = lane; c <= j; c += 32) Li[j + R * c] = df_mul(Li[j + R * c], dinv[j]);
-        __syncwarp();
-        const int rows = R - 1 - j, cols = j + 1;
-        for (int e = lane; e < rows * cols; e += 32) {
-          const int i = j + 1 + e % rows, c = e / rows;
-          Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], Li[j + R * c]));
-        }
-        __syncwarp();
-      }
-    }
-  } else {
-    for (int j = 0; j < R; ++j) {
-      for (int c = tid; c <= j; c += nt) Li[j + R * c] = df_mul(Li[j + R * c], dinv[j]);
-      __syncthreads();
-      const int rows = R - 1 - j, cols = j + 1;
-      for (int e = tid; e < rows * cols; e += nt) {
-        const int i = j + 1 + e % rows, c = e / rows;
-        Li[i + R * c] = df_sub(Li[i + R * c], df_mul(V[i + R * j], Li[j + R * c]));
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  // V^{-1} = L^{-T} L^{-1}.
-  for (int t = tid; t < R * R; t += nt) {
-    const int p = t % R, q = t / R;
-    df s0{0.f, 0.f}, s1{0.f, 0.f};
-    int i = p > q ? p : q;
-    for (; i + 1 < R; i += 2) {
-      s0 = df_add(s0, df_mul(Li[i + R * p], Li[i + R * q]));
-      s1 = df_add(s1, df_mul(Li[i + 1 + R * p], Li[i + 1 + R * q]));
-    }
-    if (i < R) s0 = df_add(s0, df_mul(Li[i + R * p], Li[i + R * q]));
-    Vi[t] = df_add(s0, s1);
-  }
-  __syncthreads();
-  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q].
+  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], Vi[p, q] = M[p * 2R + R + q].
   for (int64_t t = tid; t < In * R; t += nt) {
     const int q = int(t / In);
     const int64_t i = t - int64_t(q) * In;
     const float* g = Af + i * RS;
+    const df* vi = M + R + q;
     df s0{0.f, 0.f}, s1{0.f, 0.f};
     int p = 0;
     for (; p + 1 < R; p += 2) {
-      s0 = df_add(s0, df_mul_f(Vi[p + R * q], g[p]));
-      s1 = df_add(s1, df_mul_f(Vi[p + 1 + R * q], g[p + 1]));
+      s0 = df_add(s0, df_mul_f(vi[p * R2], g[p]));
+      s1 = df_add(s1, df_mul_f(vi[(p + 1) * R2], g[p + 1]));
     }
-    if (p < R) s0 = df_add(s0, df_mul_f(Vi[p + R * q], g[p]));
+    if (p < R) s0 = df_add(s0, df_mul_f(vi[p * R2], g[p]));
     X[i * RS + q] = df_add(s0, s1);
   }
   __syncthreads();

@@ -479,7 +479,7 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   a.nrt = p.nrt;
   a.Rpart = Rpart;
   a.Lpart = Lpart;
-  a.vec_ok = ((reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (p.J * int64_t(sizeof(T))) % 16 == 0) ? 1 : 0;
+  a.status = g_status_ptr;
   // Every rank group runs the widest group's instance; ranks beyond R are masked.
   const int RT = shape_for(prec, std::min(R, p.RTmax)).RT;
   for (int g = 0; g < p.groups; ++g) {
@@ -708,7 +708,17 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
                            int(als_smem_bytes(imax, R)));
   }
 
-  auto update = [&](int n, double* fit_out) {
+  // Finishing contraction of mode m into w.G, or nothing when it is the
+  // identity: a single remaining mode with no partial sums to add leaves
+  // X[r][i] = G[i + In r], so the update reads X itself.
+  auto finish = [&](auto right_tag, const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, const T* kr,
+                    T* Xred) -> const T* {
+    constexpr bool RIGHT = decltype(right_tag)::value;
+    if (len_o == 1 && nparts == 1) return X;
+    launch_grad<T, RIGHT>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
+    return w.G;
+  };
+  auto update = [&](int n, const T* Gn, double* fit_out) {
     ++g_launches;
     if constexpr (kDf) {
       AlsDfArgs u{};
@@ -717,13 +727,13 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.R = R;
       u.In = s.I[n];
       u.grams = reinterpret_cast<df*>(w.grams);
-      u.G = w.G;
+      u.G = Gn;
       u.An = static_cast<float*>(A[n]);
       u.lambda = lambda;
       u.status = w.h.status;
       u.fit_out = fit_out;
       u.normY2 = w.h.normY2;
-      als_update_df_kernel<<<1, kAlsThreads, als_df_smem_bytes(s.I[n], R), st>>>(u);
+      als_update_df_kernel<<<1, als_df_threads(R), als_df_smem_bytes(s.I[n], R), st>>>(u);
     } else {
       AlsArgs<T> u{};
       u.N = s.N;
@@ -731,7 +741,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.R = R;
       u.In = s.I[n];
       u.grams = w.grams;
-      u.G = w.G;
+      u.G = Gn;
       u.An = static_cast<T*>(A[n]);
       u.lambda = lambda;
       u.X = w.X;
@@ -764,8 +774,8 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
         const int64_t len_o = prod(s, 0, m), In = s.I[m];
         const T* kr = kr_vector<T>(s, Ac, R, 0, m, w.ch.kr, st);
         T* Xred = (nparts > 1 && m > 0) ? bufs[cur] : nullptr;
-        launch_grad<T, true>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
-        update(m, nullptr);
+        const T* Gm = finish(std::true_type{}, X, nparts, pstride, len_o, In, kr, Xred);
+        update(m, Gm, nullptr);
         if (m > 0) {
           const T* src = Xred ? Xred : X;
           T* dst = bufs[cur ^ 1];
@@ -788,8 +798,8 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
         const int64_t len_o = prod(s, n + 1, s.N), In = s.I[n];
         const T* kr = kr_vector<T>(s, Ac, R, n + 1, s.N, w.ch.kr, st);
         T* Xred = (nparts > 1 && n < s.N - 1) ? bufs[cur] : nullptr;
-        launch_grad<T, false>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
-        update(n, (n == s.N - 1 && fit) ? fit + it : nullptr);
+        const T* Gn = finish(std::false_type{}, X, nparts, pstride, len_o, In, kr, Xred);
+        update(n, Gn, (n == s.N - 1 && fit) ? fit + it : nullptr);
         if (n < s.N - 1) {
           const T* src = Xred ? Xred : X;
           T* dst = bufs[cur ^ 1];

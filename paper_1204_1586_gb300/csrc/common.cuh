@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "../../include/cpgrad.h"
@@ -78,7 +80,8 @@ struct LeadArgs {
   T* Rpart;                 // [nKs][R][J]  R-side partial sums (per K-split)
   T* Lpart;                 // [nJb][R][K]  L-side partial sums (per J-block)
   double* normpart;         // [nJb*nKs] partial sums of y^2, or nullptr
-  int vec_ok;               // 1: 16-byte copies are legal (J*sizeof(T) % 16 == 0, aligned Y)
+  int use_tma;              // 1: tiles arrive by TMA (set by the launcher); 0: element copies
+  int* status;              // device status word (bounded-wait timeouts)
 };
 
 // ---- cp.async (LDGSTS) wrappers ------------------------------------------------

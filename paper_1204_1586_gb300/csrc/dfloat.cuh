@@ -90,6 +90,14 @@ __device__ __forceinline__ df df_rsqrt(df a) {
   return quick_two_sum(y0, __fmul_rn(__fmul_rn(y0, e.hi), 0.5f));
 }
 
+// 1 / a for a != 0: correctly rounded FP32 reciprocal seed y0, then one Newton
+// step y = y0 + y0 (1 - a y0), the residual formed in double-float.
+__device__ __forceinline__ df df_rcp(df a) {
+  const float y0 = __frcp_rn(a.hi);
+  const df e = df_sub(df_make(1.f), df_mul_f(a, y0));
+  return quick_two_sum(y0, __fmul_rn(y0, e.hi));
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }
 
 __device__ __forceinline__ df df_from_double(double d) {

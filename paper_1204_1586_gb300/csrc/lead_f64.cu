@@ -1,6 +1,7 @@
 // FP64 instances of the CUDA-core leading contraction (Algorithm 2 steps 4/7).
 #include "lead_dispatch.cuh"
 #include "lead_simt.cuh"
+#include "tensor_map.h"
 
 namespace cpg {
 
@@ -11,7 +12,14 @@ cudaError_t run(const LeadArgs<double>& a, dim3 grid, cudaStream_t st) {
   auto kern = lead_simt_kernel<double, RT, TJ, SIDES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
   if (e != cudaSuccess) return e;
-  kern<<<grid, C::NT, C::smem_bytes, st>>>(a);
+  // Tiles by TMA (box = one 128-byte line of TK columns) where Y allows it.
+  CUtensorMap m{};
+  LeadArgs<double> b = a;
+  b.use_tma = make_matrix_map(&m, a.Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, int(sizeof(double)), a.J, a.K, uint32_t(C::SEG), uint32_t(C::TK),
+                              CU_TENSOR_MAP_SWIZZLE_128B)
+                  ? 1
+                  : 0;
+  kern<<<grid, C::NT, C::smem_bytes, st>>>(m, b);
   return cudaGetLastError();
 }
 

@@ -19,9 +19,16 @@
 // covers column chunk s / nrt and row tile s % nrt.  The R side keeps its
 // accumulators for every row of the block in registers, so it runs with
 // nrt = 1; the L side alone may use tall blocks (nrt > 1) to cut the number
-// of J-block partials.  Chunks stream through a multi-stage cp.async pipeline
-// into an XOR-swizzled shared tile that serves both access patterns without
-// bank conflicts:
+// of J-block partials.
+//
+// Tiles arrive through a ring of STAGES buffers.  When rows are whole 16-byte
+// chunks one thread issues TMA copies (cp.async.bulk.tensor, 128-byte
+// swizzle) per stage; otherwise all threads issue element copies (cp.async
+// with zero fill) into the same layout.  Entries outside Y read as zero, and
+// Khatri-Rao rows outside Y are zero, so the arithmetic needs no bounds tests.
+// The layout (tile_off) stores each 128-byte run of a column as one line whose
+// 16-byte chunks are XOR-permuted by the column index, which serves both access
+// patterns without bank conflicts:
 //   R side: warp w takes columns w, w+8, ...; each lane holds RPL rows and
 //           accumulates all RT ranks over the CTA's columns in registers.
 //   L side: warp (wr, wc) takes a band of rows and TCL columns per lane and
@@ -29,9 +36,16 @@
 //           memory once per finished column chunk.
 // Outputs are deterministic partial sums: Rpart[ks] (over K-splits) and
 // Lpart[jb] (over J-blocks), summed in a fixed order by the chain kernels.
+//
+// Every wait on a TMA barrier is bounded; on expiry the CTA records
+// CPG_ERR_TIMEOUT in the status word, waits (bounded) for its own copies and
+// returns.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace cpg {
 
@@ -41,10 +55,11 @@ struct SimtCfg {
   static constexpr bool DO_L = (SIDES & 2) != 0;
   static constexpr int NT = 256;
   static constexpr int VEC = 16 / int(sizeof(T));        // elements per 16-byte chunk
-  static constexpr int STAGE_BYTES = (TJ == 32) ? 16384 : 32768;
-  static constexpr int STAGES = (TJ == 32) ? 4 : 3;
+  static constexpr int SEG = 128 / int(sizeof(T));       // elements per 128-byte line
+  static constexpr int STAGE_BYTES = (TJ * int(sizeof(T)) <= 128) ? 16384 : 32768;
+  static constexpr int STAGES = (STAGE_BYTES == 16384) ? 4 : 3;
   static constexpr int TK = STAGE_BYTES / (TJ * int(sizeof(T)));  // columns per stage
-  static constexpr int CPC = TJ / VEC;                   // chunks per column
+  static constexpr int NSEG = TJ / SEG;                  // 128-byte lines per column
   static constexpr int RPL = TJ / 32;                    // R side: rows per lane
   static constexpr int VECR = RPL < VEC ? RPL : VEC;     // R side: elements per load
   static constexpr int NLD = RPL / VECR;                 // R side: loads per column
@@ -53,13 +68,26 @@ struct SimtCfg {
   static constexpr int WC = TK / (32 * TCL);             // L side: column groups
   static constexpr int WR = 8 / WC;                      // L side: row bands
   static constexpr int ROWS_PW = TJ / WR;                // L side: rows per warp
-  // FP32 ranks are processed in pairs (fma.rn.f32x2); FP64 ranks in chunks of VEC.
+  // FP32 products run two at a time (fma.rn.f32x2); FP64 ranks in chunks of VEC.
   static constexpr bool F2 = sizeof(T) == 4;
+  // L side, FP32, up to 20 (column, rank) accumulators per lane: a register
+  // pair holds the even-row and odd-row partial sums of one (column, rank);
+  // W_L is stored rank-major ([r][j]) so that one 16-byte load gives two row
+  // pairs of a rank.  Wider lanes keep rank pairs (W_L row-major, [j][r]).
+  static constexpr bool LP = F2 && TCL * RT <= 20;
   static_assert(F2 ? (RT % 2 == 0) : (RT % VEC == 0), "rank tile must be a multiple of the pair / vector width");
+  static_assert(TJ % SEG == 0, "row tile must hold whole 128-byte lines");
   static_assert(WC >= 1 && 8 % WC == 0, "bad L-side warp grid");
   static_assert(ROWS_PW % VEC == 0, "row band must hold whole chunks");
   static_assert(8 * RT <= STAGES * TK, "R-side reduction must fit in the tile buffers");
-  static_assert(NT % CPC == 0, "copy mapping needs whole columns per pass");
+  static_assert(NT % TK == 0 && NT % TJ == 0, "Khatri-Rao row generation maps whole rows / columns");
+  static_assert(TK <= 256 && SEG <= 256, "TMA box extent");
+
+  // Khatri-Rao entries per thread and stage: thread t generates column
+  // t % TK of W_R for ranks t / TK + u * (NT / TK), and row t % TJ of W_L for
+  // ranks t / TJ + u * (NT / TJ).
+  static constexpr int RSTEP = NT / TK, EWR = DO_R ? (RT + RSTEP - 1) / RSTEP : 1;
+  static constexpr int LSTEP = NT / TJ, EWL = DO_L ? (RT + LSTEP - 1) / LSTEP : 1;
 
   // The L-side row-band reduction reuses the stage buffer it has just consumed
   // when it fits there.
@@ -68,7 +96,8 @@ struct SimtCfg {
   static constexpr size_t wr_elems = DO_R ? size_t(2) * TK * RT : 0;
   static constexpr size_t wl_elems = DO_L ? size_t(DO_R ? 1 : 2) * TJ * RT : 0;
   static constexpr size_t red_elems = (DO_L && WR > 1 && !RED_ALIAS) ? size_t(WR) * RT * TK : 0;
-  static constexpr size_t smem_bytes = (y_elems + wr_elems + wl_elems + red_elems) * sizeof(T);
+  // + slack to align the tile ring to 1024 bytes (128-byte swizzle atoms).
+  static constexpr size_t smem_bytes = (y_elems + wr_elems + wl_elems + red_elems) * sizeof(T) + 1024;
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
   // Two CTAs per SM when both shared memory and a 128-register budget allow.
   static constexpr int MIN_BLOCKS = (SIDES != 3 && RT <= 16 && 2 * (smem_bytes + 1024) <= 228 * 1024) ? 2 : 1;
@@ -108,10 +137,13 @@ __device__ __forceinline__ void lds_pairs(const float* row, uint64_t (&w)[NP]) {
   }
 }
 
-// Swizzled position of element (c, j) inside one stage of the tile.
-template <int TJ, int VEC>
+// Position of element (column c, row j) inside one stage of the tile: line
+// j / SEG of every column forms a TK x 128-byte block (one TMA box of the
+// 128-byte-swizzle mode), and the 16-byte chunk index within a line is XORed
+// with c mod 8.
+template <int TK, int SEG, int VEC>
 __device__ __forceinline__ int tile_off(int c, int j) {
-  return c * TJ + (((j / VEC) ^ (c & 7)) * VEC) + (j % VEC);
+  return (j / SEG) * (TK * SEG) + c * SEG + ((((j % SEG) / VEC) ^ (c & 7)) * VEC) + (j % VEC);
 }
 
 template <typename T, int N>
@@ -148,19 +180,35 @@ __device__ __forceinline__ void sts_vec(T* p, const T (&in)[N]) {
   }
 }
 
+// Element copy global -> shared with zero fill: src_bytes = 0 writes zeros
+// and reads nothing.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, int src_bytes) {
+  static_assert(BYTES == 4 || BYTES == 8, "element copy is 4 or 8 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES),
+               "r"(src_bytes)
+               : "memory");
+}
+
 // SIDES: bit 0 = R side (step 4), bit 1 = L side (step 7).
+// tmap: Y as the 2-D tensor {J, K} (rows contiguous), box {SEG, TK}, 128-byte
+// swizzle, zero fill; used when a.use_tma is set.
 template <typename T, int RT, int TJ, int SIDES>
 __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
-    lead_simt_kernel(const LeadArgs<T> a) {
+    lead_simt_kernel(const __grid_constant__ CUtensorMap tmap, const LeadArgs<T> a) {
   using C = SimtCfg<T, RT, TJ, SIDES>;
   constexpr bool DO_R = C::DO_R, DO_L = C::DO_L;
-  constexpr int NT = C::NT, VEC = C::VEC, TK = C::TK, STAGES = C::STAGES;
+  constexpr int NT = C::NT, VEC = C::VEC, TK = C::TK, STAGES = C::STAGES, SEG = C::SEG;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ys = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ unsigned char smem_dyn[];
+  // Align by an offset from the shared-memory base (not through an integer
+  // round trip), so that accesses keep the shared state space.
+  T* Ys = reinterpret_cast<T*>(smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u));
   T* WRs = Ys + C::y_elems;
   T* WLs = WRs + C::wr_elems;
   T* red_sep = WLs + C::wl_elems;
+  __shared__ uint64_t bar_full[STAGES];
+  __shared__ int abort_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t J = a.J, K = a.K;
@@ -173,121 +221,117 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   const int nchunk = int((kend - kbeg + TK - 1) / TK);
   const int nst = nchunk * nrt;
   const bool do_norm = DO_R && (a.normpart != nullptr);
+  const bool use_tma = a.use_tma != 0;
 
-  // Skipped (out-of-range) tile entries must read as finite values: zero once.
-  for (int f = tid; f < int(C::y_elems); f += NT) Ys[f] = T(0);
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) tc::mbar_init(&bar_full[s], 1);
+    tc::mbar_fence_init();
+    abort_flag = 0;
+  }
 
-  // Copy mapping: thread tid always moves chunk q = tid % CPC of columns
-  // tid / CPC + u * (NT / CPC), so its addresses advance by fixed strides.
-  constexpr int CSTEP = NT / C::CPC;                // columns per copy pass
-  const int cq = tid % C::CPC, cc0 = tid / C::CPC;
+  // Stage `it` (column chunk it / nrt, row tile it % nrt) into buffer it % STAGES.
+  int issued = 0;  // stages issued so far
   auto issue = [&](int it) {
-    if (it < nst) {
-      T* dst = Ys + size_t(it % STAGES) * TK * TJ;
-      const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
-      const int64_t j0 = jblk + int64_t(it % nrt) * TJ;
-      if (a.vec_ok) {
-        const int64_t jg = j0 + int64_t(cq) * VEC;
-        if (jg < J) {
-          const T* src = a.Y + jg + J * (cbase + cc0);
-          const int64_t cstride = J * CSTEP;
-          const int64_t nc = kend - cbase;          // valid columns in this chunk
+    if (it >= nst) return;
+    issued = it + 1;
+    T* dst = Ys + size_t(it % STAGES) * TK * TJ;
+    const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
+    const int64_t j0 = jblk + int64_t(it % nrt) * TJ;
+    if (use_tma) {
+      if (tid == 0) {
+        tc::fence_async_smem();
+        uint64_t* bar = &bar_full[it % STAGES];
+        tc::mbar_arrive_expect_tx(bar, uint32_t(C::STAGE_BYTES));
 #pragma unroll
-          for (int u = 0; u < TK / CSTEP; ++u) {
-            const int c = cc0 + u * CSTEP;
-            if (c < nc) cp_async16(dst + c * TJ + ((cq ^ (c & 7)) * VEC), src);
-            src += cstride;
-          }
+        for (int s = 0; s < C::NSEG; ++s)
+          tc::tma_load_2d(dst + s * TK * SEG, &tmap, int(j0) + s * SEG, int(cbase), bar);
+      }
+    } else {
+#pragma unroll 4
+      for (int f = tid; f < TK * TJ; f += NT) {
+        const int c = f / TJ, j = f % TJ;
+        const int64_t cg = cbase + c, jg = j0 + j;
+        const bool in = cg < K && jg < J;
+        cp_async_zfill<int(sizeof(T))>(dst + tile_off<TK, SEG, VEC>(c, j), in ? a.Y + jg + J * cg : a.Y,
+                                       in ? int(sizeof(T)) : 0);
+      }
+      cp_async_commit();
+    }
+  };
+
+  // ---- Khatri-Rao rows ----
+  const int cw = tid % TK, rw = tid / TK;  // W_R: column cw, ranks rw + RSTEP * u
+  const int jw = tid % TJ, rl = tid / TJ;  // W_L: row jw, ranks rl + LSTEP * u
+  T pwa[C::EWR], pwq[C::EWR], pla[C::EWL], plq[C::EWL];
+  // Loads (not yet products) of the rows of `kr` at index idx (< lim) for
+  // ranks rbase + rstep * u: one division per thread and stage.
+  auto fetch_rows = [&](const KrRows<T>& kr, int64_t idx, int64_t lim, int rbase, int rstep, auto ne_tag, T* fa,
+                        T* fq) {
+    constexpr int NE = decltype(ne_tag)::value;
+    const bool in = idx < lim;
+    uint32_t i = 0, q = 0;
+    if (in && kr.A != nullptr) {
+      q = kr.d.div(uint32_t(idx));
+      i = uint32_t(idx) - q * kr.d.d;
+    }
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      const int r = rbase + rstep * u;
+      if (in && r < RT && r0 + r < R) {
+        if (kr.A == nullptr) {
+          fa[u] = T(1);
+          fq[u] = T(1);
+        } else {
+          fa[u] = kr.A[i + int64_t(kr.d.d) * (r0 + r)];
+          fq[u] = (kr.Q != nullptr) ? kr.Q[q + kr.ldq * (r0 + r)] : T(1);
         }
       } else {
-        for (int f = tid; f < TK * TJ; f += NT) {
-          const int c = f / TJ, j = f % TJ;
-          const int64_t cg = cbase + c, jg = j0 + j;
-          if (cg < kend && jg < J) cp_async_small<int(sizeof(T))>(dst + tile_off<TJ, VEC>(c, j), a.Y + jg + J * cg);
-        }
+        fa[u] = T(0);
+        fq[u] = T(0);
       }
     }
-    cp_async_commit();
   };
-  // W_L rows of row tile `rt` (Khatri-Rao over modes [0, k)).
-  auto gen_wl = [&](T* dst, int rt) {
-    const int64_t j0 = jblk + int64_t(rt) * TJ;
-    for (int f = tid; f < TJ * RT; f += NT) {
-      const int j = f / RT, r = f % RT;
-      const int64_t jg = j0 + j;
-      dst[f] = (jg < J && r0 + r < R) ? a.wl.at(uint32_t(jg), r0 + r) : T(0);
-    }
-  };
-  // Register staging of one stage's Khatri-Rao entries (f = tid + NT*u).
-  constexpr int EWR = DO_R ? (TK * RT + NT - 1) / NT : 1;
-  constexpr int EWL = (DO_L && !DO_R) ? (TJ * RT + NT - 1) / NT : 1;
-  T pwa[EWR], pwq[EWR], pla[EWL], plq[EWL];
   auto fetch_wr = [&](int it2) {
-    const int64_t cb = kbeg + int64_t(it2 / nrt) * TK;
-#pragma unroll
-    for (int u = 0; u < EWR; ++u) {
-      const int f = tid + NT * u;
-      const int c = f / RT, r = f % RT;
-      const int64_t cg = cb + c;
-      if (it2 < nst && f < TK * RT && cg < kend && r0 + r < R) {
-        a.wr.fetch(uint32_t(cg), r0 + r, pwa[u], pwq[u]);
-      } else {
-        pwa[u] = T(0);
-        pwq[u] = T(0);
-      }
-    }
+    if (it2 < nst)
+      fetch_rows(a.wr, kbeg + int64_t(it2 / nrt) * TK + cw, K, rw, C::RSTEP,
+                 std::integral_constant<int, C::EWR>{}, pwa, pwq);
   };
   auto store_wr = [&](int it2) {
     T* Wr = WRs + size_t(it2 & 1) * TK * RT;
 #pragma unroll
-    for (int u = 0; u < EWR; ++u) {
-      const int f = tid + NT * u;
-      if (f < TK * RT) Wr[f] = pwa[u] * pwq[u];
+    for (int u = 0; u < C::EWR; ++u) {
+      const int r = rw + C::RSTEP * u;
+      if (r < RT) Wr[cw * RT + r] = pwa[u] * pwq[u];
     }
   };
   auto fetch_wl = [&](int it2) {
-    const int64_t j0 = jblk + int64_t(it2 % nrt) * TJ;
+    if (it2 < nst)
+      fetch_rows(a.wl, jblk + int64_t(it2 % nrt) * TJ + jw, J, rl, C::LSTEP,
+                 std::integral_constant<int, C::EWL>{}, pla, plq);
+  };
+  auto store_wl = [&](T* Wl) {
 #pragma unroll
-    for (int u = 0; u < EWL; ++u) {
-      const int f = tid + NT * u;
-      const int j = f / RT, r = f % RT;
-      const int64_t jg = j0 + j;
-      if (it2 < nst && f < TJ * RT && jg < J && r0 + r < R) {
-        a.wl.fetch(uint32_t(jg), r0 + r, pla[u], plq[u]);
-      } else {
-        pla[u] = T(0);
-        plq[u] = T(0);
-      }
+    for (int u = 0; u < C::EWL; ++u) {
+      const int r = rl + C::LSTEP * u;
+      if (r < RT) Wl[C::LP ? r * TJ + jw : jw * RT + r] = pla[u] * plq[u];
     }
   };
-  auto store_wl = [&](int it2) {
-    T* Wl = WLs + size_t(it2 & 1) * TJ * RT;
-#pragma unroll
-    for (int u = 0; u < EWL; ++u) {
-      const int f = tid + NT * u;
-      if (f < TJ * RT) Wl[f] = pla[u] * plq[u];
-    }
-  };
+  const bool wl_per_stage = DO_L && !DO_R && nrt > 1;
   if constexpr (DO_L) {
-    if (nrt == 1) gen_wl(WLs, 0);
+    fetch_wl(0);
+    store_wl(WLs);
   }
   if constexpr (DO_R) {
     fetch_wr(0);
     store_wr(0);
   }
-  if constexpr (DO_L && !DO_R) {
-    if (nrt > 1) {
-      fetch_wl(0);
-      store_wl(0);
-    }
-  }
-  __syncthreads();
+  __syncthreads();  // barriers initialised, first Khatri-Rao rows stored
 
   constexpr int NP = RT / 2;  // rank pairs (FP32)
-  T racc[C::NLD][C::VECR][(DO_R && !C::F2) ? RT : 1];  // FP64 accumulators
+  T racc[C::NLD][C::VECR][(DO_R && !C::F2) ? RT : 1];                          // FP64 accumulators
   T lacc[C::TCL][DO_L ? RT : 1];
-  uint64_t racc2[C::NLD][C::VECR][(DO_R && C::F2) ? NP : 1];
-  uint64_t lacc2[C::TCL][(DO_L && C::F2) ? NP : 1];
+  uint64_t racc2[C::NLD][C::VECR][(DO_R && C::F2) ? NP : 1];              // rank pairs
+  uint64_t lacc2[C::TCL][(DO_L && C::F2) ? (C::LP ? RT : NP) : 1];         // row pairs (LP) or rank pairs
   T ss = T(0);  // this thread's sum of y^2 (fixed order); summed in FP64 across threads
   if constexpr (DO_R) {
 #pragma unroll
@@ -308,7 +352,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     for (int t = 0; t < C::TCL; ++t) {
       if constexpr (C::F2) {
 #pragma unroll
-        for (int r = 0; r < NP; ++r) lacc2[t][r] = 0ull;
+        for (int r = 0; r < (C::LP ? RT : NP); ++r) lacc2[t][r] = 0ull;
       } else {
 #pragma unroll
         for (int r = 0; r < RT; ++r) lacc[t][r] = T(0);
@@ -324,109 +368,145 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
 #pragma unroll 1
   for (int s = 0; s < STAGES - 1; ++s) issue(s);
 
+  int ci = 0, rt = 0;  // column chunk and row tile of stage it
 #pragma unroll 1
   for (int it = 0; it < nst; ++it) {
-    cp_async_wait<STAGES - 2>();
-    const int ci = it / nrt, rt = it % nrt;
+    // One thread waits for the TMA barrier (acquiring the copied tile) and the
+    // block barrier orders every other thread after it, so that 255 threads do
+    // not poll shared memory while the tile is in flight.
+    if (use_tma) {
+      if (tid == 0 && !tc::mbar_wait(&bar_full[it % STAGES], uint32_t(it / STAGES) & 1u)) abort_flag = 1;
+    } else {
+      cp_async_wait<STAGES - 2>();
+    }
+    __syncthreads();  // stage it is complete for every thread; stage it - 1 is consumed
+    if (abort_flag) break;
     const int64_t cbase = kbeg + int64_t(ci) * TK;
-    __syncthreads();
     issue(it + STAGES - 1);
     // Khatri-Rao rows of the next stage: loads now, products stored after this
     // stage's arithmetic (into the buffer the previous stage used).
     if constexpr (DO_R) fetch_wr(it + 1);
-    if constexpr (DO_L && !DO_R) {
-      if (nrt > 1) fetch_wl(it + 1);
-    }
+    if (wl_per_stage) fetch_wl(it + 1);
 
     T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
     if constexpr (DO_R) {
+      // Lane: RPL rows (one 16-byte chunk per load); pairs hold two ranks of a row.
       const T* Wr = WRs + size_t(it & 1) * TK * RT;
 #pragma unroll 2
       for (int i = 0; i < C::CPW; ++i) {
         const int c = warp + 8 * i;
-        if (cbase + c < kend) {
-          T y[C::NLD][C::VECR];
+        T y[C::NLD][C::VECR];
 #pragma unroll
-          for (int m = 0; m < C::NLD; ++m) {
-            const int j = lane * C::VECR + 32 * C::VECR * m;
-            lds_vec<T, C::VECR>(Yst + tile_off<TJ, VEC>(c, j), y[m]);
-          }
-          if constexpr (C::F2) {
-            uint64_t yy[C::NLD][C::VECR];
+        for (int m = 0; m < C::NLD; ++m) {
+          const int j = lane * C::VECR + 32 * C::VECR * m;
+          lds_vec<T, C::VECR>(Yst + tile_off<TK, SEG, VEC>(c, j), y[m]);
+        }
+        if constexpr (C::F2) {
+          uint64_t yy[C::NLD][C::VECR];
 #pragma unroll
-            for (int m = 0; m < C::NLD; ++m)
+          for (int m = 0; m < C::NLD; ++m)
 #pragma unroll
-              for (int e = 0; e < C::VECR; ++e) yy[m][e] = f2_pack(float(y[m][e]), float(y[m][e]));
-            uint64_t w[NP];
-            lds_pairs<NP>(reinterpret_cast<const float*>(Wr) + c * RT, w);
+            for (int e = 0; e < C::VECR; ++e) yy[m][e] = f2_pack(float(y[m][e]), float(y[m][e]));
+          uint64_t w[NP];
+          lds_pairs<NP>(reinterpret_cast<const float*>(Wr) + c * RT, w);
 #pragma unroll
-            for (int r = 0; r < NP; ++r)
-#pragma unroll
-              for (int m = 0; m < C::NLD; ++m)
-#pragma unroll
-                for (int e = 0; e < C::VECR; ++e) racc2[m][e][r] = f2_fma(yy[m][e], w[r], racc2[m][e][r]);
-          } else {
-#pragma unroll
-            for (int r4 = 0; r4 < RT; r4 += VEC) {
-              T w[VEC];
-              lds_vec<T, VEC>(Wr + c * RT + r4, w);
-#pragma unroll
-              for (int m = 0; m < C::NLD; ++m)
-#pragma unroll
-                for (int e = 0; e < C::VECR; ++e)
-#pragma unroll
-                  for (int v = 0; v < VEC; ++v) racc[m][e][r4 + v] = fma(y[m][e], w[v], racc[m][e][r4 + v]);
-            }
-          }
-          if (do_norm) {
+          for (int r = 0; r < NP; ++r)
 #pragma unroll
             for (int m = 0; m < C::NLD; ++m)
 #pragma unroll
-              for (int e = 0; e < C::VECR; ++e) ss = fma(y[m][e], y[m][e], ss);
+              for (int e = 0; e < C::VECR; ++e) racc2[m][e][r] = f2_fma(yy[m][e], w[r], racc2[m][e][r]);
+        } else {
+#pragma unroll
+          for (int r4 = 0; r4 < RT; r4 += VEC) {
+            T w[VEC];
+            lds_vec<T, VEC>(Wr + c * RT + r4, w);
+#pragma unroll
+            for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+              for (int e = 0; e < C::VECR; ++e)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) racc[m][e][r4 + v] = fma(y[m][e], w[v], racc[m][e][r4 + v]);
           }
+        }
+        if (do_norm) {
+#pragma unroll
+          for (int m = 0; m < C::NLD; ++m)
+#pragma unroll
+            for (int e = 0; e < C::VECR; ++e) ss = fma(y[m][e], y[m][e], ss);
         }
       }
     }
 
     if constexpr (DO_L) {
-      const T* Wl = WLs + ((!DO_R && nrt > 1) ? size_t(it & 1) * TJ * RT : 0);
+      const T* Wl = WLs + (wl_per_stage ? size_t(it & 1) * TJ * RT : 0);
+      // Lanes read 16-byte chunks of consecutive columns at the same rows: the
+      // XOR permutation puts 8 consecutive columns on 8 distinct bank groups.
+      if constexpr (C::LP) {
 #pragma unroll 2
-      for (int q = 0; q < C::ROWS_PW / VEC; ++q) {
-        const int jl = wr * C::ROWS_PW + q * VEC;
-        const int qc = jl / VEC;
-        T y[C::TCL][VEC];
+        for (int q = 0; q < C::ROWS_PW / VEC; ++q) {
+          const int jl = wr * C::ROWS_PW + q * VEC;
+          uint64_t yq[C::TCL][2];  // rows (jl, jl+1) and (jl+2, jl+3) of each column
 #pragma unroll
-        for (int t = 0; t < C::TCL; ++t) {
-          const int c = cl0 + 32 * t;
-          lds_vec<T, VEC>(Yst + c * TJ + ((qc ^ (c & 7)) * VEC), y[t]);
+          for (int t = 0; t < C::TCL; ++t) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Yst + tile_off<TK, SEG, VEC>(cl0 + 32 * t, jl));
+            yq[t][0] = v.x;
+            yq[t][1] = v.y;
+          }
+          const T* wl = Wl + jl;  // rank-major: W_L[j][r] at r * TJ + j
+#pragma unroll
+          for (int r = 0; r < RT; ++r) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(wl + r * TJ);
+#pragma unroll
+            for (int t = 0; t < C::TCL; ++t) {
+              lacc2[t][r] = f2_fma(yq[t][0], w.x, lacc2[t][r]);
+              lacc2[t][r] = f2_fma(yq[t][1], w.y, lacc2[t][r]);
+            }
+          }
         }
+      } else {
+#pragma unroll 2
+        for (int q = 0; q < C::ROWS_PW / VEC; ++q) {
+          const int jl = wr * C::ROWS_PW + q * VEC;
+          T y[C::TCL][VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          if constexpr (C::F2) {
-            uint64_t yy[C::TCL];
+          for (int t = 0; t < C::TCL; ++t) lds_vec<T, VEC>(Yst + tile_off<TK, SEG, VEC>(cl0 + 32 * t, jl), y[t]);
 #pragma unroll
-            for (int t = 0; t < C::TCL; ++t) yy[t] = f2_pack(float(y[t][e]), float(y[t][e]));
-            uint64_t w[NP];
-            lds_pairs<NP>(reinterpret_cast<const float*>(Wl) + (jl + e) * RT, w);
+          for (int e = 0; e < VEC; ++e) {
+            if constexpr (C::F2) {
+              uint64_t yy[C::TCL];
 #pragma unroll
-            for (int r = 0; r < NP; ++r)
+              for (int t = 0; t < C::TCL; ++t) yy[t] = f2_pack(float(y[t][e]), float(y[t][e]));
+              uint64_t w[NP];
+              lds_pairs<NP>(reinterpret_cast<const float*>(Wl) + (jl + e) * RT, w);
 #pragma unroll
-              for (int t = 0; t < C::TCL; ++t) lacc2[t][r] = f2_fma(yy[t], w[r], lacc2[t][r]);
-          } else {
+              for (int r = 0; r < NP; ++r)
 #pragma unroll
-            for (int r4 = 0; r4 < RT; r4 += VEC) {
-              T w[VEC];
-              lds_vec<T, VEC>(Wl + (jl + e) * RT + r4, w);
+                for (int t = 0; t < C::TCL; ++t) lacc2[t][r] = f2_fma(yy[t], w[r], lacc2[t][r]);
+            } else {
 #pragma unroll
-              for (int t = 0; t < C::TCL; ++t)
+              for (int r4 = 0; r4 < RT; r4 += VEC) {
+                T w[VEC];
+                lds_vec<T, VEC>(Wl + (jl + e) * RT + r4, w);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) lacc[t][r4 + v] = fma(y[t][e], w[v], lacc[t][r4 + v]);
+                for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+                  for (int v = 0; v < VEC; ++v) lacc[t][r4 + v] = fma(y[t][e], w[v], lacc[t][r4 + v]);
+              }
             }
           }
         }
       }
       if (rt == nrt - 1) {
-        if constexpr (C::F2) {
+        if constexpr (C::LP) {
+#pragma unroll
+          for (int t = 0; t < C::TCL; ++t)
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+              float a0, a1;
+              f2_unpack(lacc2[t][r], a0, a1);
+              lacc[t][r] = a0 + a1;  // even rows + odd rows
+            }
+        } else if constexpr (C::F2) {
 #pragma unroll
           for (int t = 0; t < C::TCL; ++t)
 #pragma unroll
@@ -454,6 +534,8 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
             const int64_t cg = cbase + c;
             if (r0 + r < R && cg < kend) a.Lpart[(int64_t(jb) * R + r0 + r) * K + cg] = sum;
           }
+          // This buffer is refilled by TMA (the async proxy) after the next barrier.
+          if constexpr (C::RED_ALIAS) tc::fence_async_smem();
         } else {
 #pragma unroll
           for (int t = 0; t < C::TCL; ++t) {
@@ -469,13 +551,25 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     if constexpr (DO_R) {
       if (it + 1 < nst) store_wr(it + 1);
     }
-    if constexpr (DO_L && !DO_R) {
-      if (nrt > 1 && it + 1 < nst) store_wl(it + 1);
+    if (wl_per_stage && it + 1 < nst) store_wl(WLs + size_t((it + 1) & 1) * TJ * RT);
+    if (++rt == nrt) {
+      rt = 0;
+      ++ci;
     }
   }
 
-  cp_async_wait<0>();
-  __syncthreads();
+  if (!use_tma) cp_async_wait<0>();
+  __syncthreads();  // every thread has left the loop
+  if (abort_flag) {
+    if (tid == 0) {
+      atomicCAS(a.status, 0, int(CPG_ERR_TIMEOUT));
+      // Let this CTA's own copies land (bounded) before its memory is released:
+      // the newest phase of every stage buffer (older phases have completed).
+      for (int q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+        tc::mbar_wait(&bar_full[q % STAGES], uint32_t(q / STAGES) & 1u, 1u << 16);
+    }
+    return;
+  }
 
   if constexpr (DO_R) {
     // Sum the 8 warps' column-split partials through the (now idle) tile buffers.
@@ -513,7 +607,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
       __syncthreads();
-      double* wsum = reinterpret_cast<double*>(smem_raw);
+      double* wsum = reinterpret_cast<double*>(Ys);
       if (lane == 0) wsum[warp] = sd;
       __syncthreads();
       if (tid == 0) {

@@ -1,37 +1,16 @@
 // Host side of the tensor-core leading contraction: TMA tensor map of Y and
 // the kernel instances (rank tile 16 / 32 / 64, sides, BF16x3 or BF16).
-#include <cudaTypedefs.h>
-
 #include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
+#include "tensor_map.h"
 
 namespace cpg {
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (fn == nullptr) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 // Y as a 2-D tensor [K][J] (J contiguous); one box = 128 rows x 64 columns.
 bool make_y_map(CUtensorMap* m, const float* Y, int64_t J, int64_t K) {
-  auto fn = encode_fn();
-  if (fn == nullptr) return false;
-  const cuuint64_t dims[2] = {cuuint64_t(J), cuuint64_t(K)};
-  const cuuint64_t strides[1] = {cuuint64_t(J) * sizeof(float)};
-  const cuuint32_t box[2] = {128, 64};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Y), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return make_matrix_map(m, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J, K, 128, 64, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 template <int RTP, int SIDES, int PREC>
@@ -70,7 +49,7 @@ int tc_max_nrt(int RTP, int sides, int prec) {
 }
 
 bool tc_eligible(const float* Y, int64_t J) {
-  return (reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (J % 4) == 0 && encode_fn() != nullptr;
+  return (reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (J % 4) == 0 && tensor_map_encoder() != nullptr;
 }
 
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {

@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   constexpr bool DO_R = C::DO_R, DO_L = C::DO_L, X3 = C::X3;
   constexpr int NT = C::NT;
   extern __shared__ unsigned char smem_dyn[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  // Align by an offset from the shared-memory base (not through an integer
+  // round trip), so that accesses keep the shared state space.
+  unsigned char* sm = smem_dyn + ((1024u - (tc::smem_addr(smem_dyn) & 1023u)) & 1023u);
   __shared__ uint64_t bar_full[C::NB];
   __shared__ uint64_t bar_mma[C::NB];
   __shared__ uint32_t tslot;
