@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "als.cuh"
 #include "als_df.cuh"
@@ -99,7 +100,9 @@ struct LeadPlan {
   size_t rpart_elems = 0, lpart_elems = 0;
 };
 
-SimtShape shape_for(int prec, int r) { return is_f64(prec) ? simt_shape_f64(r) : simt_shape_f32(r); }
+SimtShape shape_for(int prec, int r, int sides) {
+  return is_f64(prec) ? simt_shape_f64(r, sides) : simt_shape_f32(r, sides);
+}
 
 bool is_tc_prec(int prec) { return prec == CPG_BF16X3 || prec == CPG_BF16; }
 
@@ -127,6 +130,52 @@ void choose_ksplit(LeadPlan& p, int slots) {
   }
   p.nKs = best_ks;
   p.Kc = ((chunks + p.nKs - 1) / p.nKs) * p.TK;
+}
+
+// Grid of a CUDA-core leading pass: J-blocks of nrt row tiles (the L side
+// alone may take several; with the R side nrt = 1) times K-splits of `per`
+// column chunks.  Minimises, in units of one stage's time on a full GPU,
+//   waves * (stages per CTA + 1.5) + (partial-sum bytes written and read back)
+// over the distinct (nrt, per) pairs; `slots` = resident CTAs on the GPU.
+void choose_grid(LeadPlan& p, int R, int esize, int slots) {
+  const int64_t tiles = (p.J + p.TJ - 1) / p.TJ;
+  const int64_t chunks = (p.K + p.TK - 1) / p.TK;
+  const double stage_bytes = double(p.TJ) * p.TK * esize;
+  double best = 1e300;
+  int64_t best_nrt = 1, best_per = chunks;
+  auto consider = [&](int64_t nrt, int64_t per) {
+    const int64_t nJb = (tiles + nrt - 1) / nrt, nKs = (chunks + per - 1) / per;
+    const int64_t units = nJb * nKs;
+    if (nJb > 65535 || nKs > 65535) return;
+    const double waves = double((units + slots - 1) / slots);
+    double partial = 0.0;
+    if (p.sides & 1) partial += 2.0 * double(nKs) * R * double(p.J) * esize;
+    if (p.sides & 2) partial += 2.0 * double(nJb) * R * double(p.K) * esize;
+    const double cost = waves * (double(per * nrt) + 1.5) + partial / (double(slots) * stage_bytes);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_nrt = nrt;
+      best_per = per;
+    }
+  };
+  // Distinct values of ceil(n / d) for d = 1..n (about 2 sqrt(n) of them).
+  auto distinct_ceils = [](int64_t n) {
+    std::vector<int64_t> v;
+    for (int64_t d = 1; d <= n;) {
+      const int64_t q = (n + d - 1) / d;
+      v.push_back(q);
+      d = (q > 1) ? (n + q - 2) / (q - 1) : n + 1;  // next d with a smaller quotient
+    }
+    return v;
+  };
+  const std::vector<int64_t> nrts = (p.sides == 2) ? distinct_ceils(tiles) : std::vector<int64_t>{1};
+  const std::vector<int64_t> pers = distinct_ceils(chunks);
+  for (int64_t nrt : nrts)
+    for (int64_t per : pers) consider(nrt, per);
+  p.nrt = int(best_nrt);
+  p.nJb = int((tiles + best_nrt - 1) / best_nrt);
+  p.nKs = int((chunks + best_per - 1) / best_per);
+  p.Kc = best_per * p.TK;
 }
 
 LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
@@ -165,42 +214,11 @@ LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
   p.RTmax = is_f64(prec) ? kMaxRankTileF64 : kMaxRankTileF32;
   p.groups = (R + p.RTmax - 1) / p.RTmax;
   // All rank groups share one tile geometry: the widest group's.
-  const SimtShape sh = shape_for(prec, std::min(R, p.RTmax));
+  const SimtShape sh = shape_for(prec, std::min(R, p.RTmax), sides);
   p.TJ = sh.TJ;
   p.TK = sh.TK;
-  if (sides == 2) {
-    // L side alone: tall J-blocks (about 2048 rows) keep the J-block partials few.
-    const int64_t tiles = (p.J + p.TJ - 1) / p.TJ;
-    p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, std::max(1, 2048 / p.TJ))));
-  } else {
-    p.nrt = 1;
-  }
-  const int64_t jrows = int64_t(p.TJ) * p.nrt;
-  p.nJb = int((p.J + jrows - 1) / jrows);
-  const int64_t chunks = (p.K + p.TK - 1) / p.TK;
   const int bps = is_f64(prec) ? lead_blocks_per_sm_f64(sh.RT, sides) : lead_blocks_per_sm_f32(sh.RT, sides);
-  const int slots = num_sms() * std::max(bps, 1);
-  double best = -1.0;
-  int best_ks = 1;
-  const int64_t max_ks = std::min<int64_t>(chunks, 4096);
-  for (int64_t ks = 1; ks <= max_ks; ++ks) {
-    const int64_t per = (chunks + ks - 1) / ks;  // chunks per CTA
-    const int64_t nks = (chunks + per - 1) / per;
-    if (nks != ks) continue;
-    const int64_t units = int64_t(p.nJb) * nks;
-    if (units > 65535LL * 64) break;
-    const int64_t waves = (units + slots - 1) / slots;
-    const double eff = double(units) / double(waves * slots);
-    const double stages = double(per * p.nrt);
-    const double score = eff * stages / (stages + 1.5);
-    if (score > best + 1e-9) {
-      best = score;
-      best_ks = int(nks);
-    }
-  }
-  p.nKs = best_ks;
-  const int64_t per = (chunks + p.nKs - 1) / p.nKs;
-  p.Kc = per * p.TK;
+  choose_grid(p, R, is_f64(prec) ? 8 : 4, num_sms() * std::max(bps, 1));
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
   p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
   return p;
@@ -481,7 +499,7 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   a.Lpart = Lpart;
   a.status = g_status_ptr;
   // Every rank group runs the widest group's instance; ranks beyond R are masked.
-  const int RT = shape_for(prec, std::min(R, p.RTmax)).RT;
+  const int RT = shape_for(prec, std::min(R, p.RTmax), p.sides).RT;
   for (int g = 0; g < p.groups; ++g) {
     a.r0 = g * p.RTmax;
     a.normpart = (g == 0) ? normpart : nullptr;

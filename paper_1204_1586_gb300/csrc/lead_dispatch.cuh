@@ -11,9 +11,10 @@ struct SimtShape {
   size_t smem;
 };
 
-// Smallest supported rank tile >= r (r <= max tile), its row tile TJ and columns per stage TK.
-SimtShape simt_shape_f32(int r);
-SimtShape simt_shape_f64(int r);
+// Smallest supported rank tile >= r (r <= max tile), and the row tile TJ and
+// columns per stage TK of its instance for `sides`.
+SimtShape simt_shape_f32(int r, int sides);
+SimtShape simt_shape_f64(int r, int sides);
 constexpr int kMaxRankTileF32 = 64;
 constexpr int kMaxRankTileF64 = 16;
 

@@ -23,11 +23,14 @@ cudaError_t run(const LeadArgs<float>& a, dim3 grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int RT, int TJ>
+// TJ: row tile of the R-side and fused instances; TJL: of the L-side-only
+// instance (half-height tiles at small ranks: twice the columns per stage, so
+// half the Khatri-Rao rows regenerated per stage of tall J-blocks).
+template <int RT, int TJ, int TJL>
 cudaError_t run_sides(const LeadArgs<float>& a, int sides, dim3 grid, cudaStream_t st) {
   switch (sides) {
     case 1: return run<RT, TJ, 1>(a, grid, st);
-    case 2: return run<RT, TJ, 2>(a, grid, st);
+    case 2: return run<RT, TJL, 2>(a, grid, st);
     case 3: return run<RT, TJ, 3>(a, grid, st);
     default: return cudaErrorInvalidValue;
   }
@@ -46,59 +49,51 @@ int bps() {
   return n;
 }
 
-template <int RT, int TJ>
+template <int RT, int TJ, int TJL>
 int bps_sides(int sides) {
   static int cache[4] = {0, 0, 0, 0};
   if (sides < 1 || sides > 3) return 1;
-  if (cache[sides] == 0) cache[sides] = sides == 1 ? bps<RT, TJ, 1>() : sides == 2 ? bps<RT, TJ, 2>() : bps<RT, TJ, 3>();
+  if (cache[sides] == 0)
+    cache[sides] = sides == 1 ? bps<RT, TJ, 1>() : sides == 2 ? bps<RT, TJL, 2>() : bps<RT, TJ, 3>();
   return cache[sides];
 }
 
-template <int RT, int TJ>
-SimtShape shape() {
+template <int RT, int TJ, int TJL>
+SimtShape shape(int sides) {
   using C = SimtCfg<float, RT, TJ, 3>;
-  return SimtShape{RT, TJ, C::TK, C::smem_bytes};
+  using CL = SimtCfg<float, RT, TJL, 2>;
+  return sides == 2 ? SimtShape{RT, TJL, CL::TK, CL::smem_bytes} : SimtShape{RT, TJ, C::TK, C::smem_bytes};
 }
 }  // namespace
 
-SimtShape simt_shape_f32(int r) {
-  if (r <= 4) return shape<4, 256>();
-  if (r <= 8) return shape<8, 256>();
-  if (r <= 10) return shape<10, 128>();
-  if (r <= 12) return shape<12, 128>();
-  if (r <= 16) return shape<16, 128>();
-  if (r <= 24) return shape<24, 64>();
-  if (r <= 32) return shape<32, 64>();
-  if (r <= 48) return shape<48, 32>();
-  return shape<64, 32>();
+#define CPG_F32_INSTANCES(X) \
+  X(4, 256, 128) X(8, 256, 128) X(10, 128, 64) X(12, 128, 64) X(16, 128, 64) X(24, 64, 64) X(32, 64, 64) \
+  X(48, 32, 32) X(64, 32, 32)
+
+SimtShape simt_shape_f32(int r, int sides) {
+#define CPG_SHAPE(RT, TJ, TJL) \
+  if (r <= RT) return shape<RT, TJ, TJL>(sides);
+  CPG_F32_INSTANCES(CPG_SHAPE)
+#undef CPG_SHAPE
+  return shape<64, 32, 32>(sides);
 }
 
 int lead_blocks_per_sm_f32(int RT, int sides) {
   switch (RT) {
-    case 4: return bps_sides<4, 256>(sides);
-    case 8: return bps_sides<8, 256>(sides);
-    case 10: return bps_sides<10, 128>(sides);
-    case 12: return bps_sides<12, 128>(sides);
-    case 16: return bps_sides<16, 128>(sides);
-    case 24: return bps_sides<24, 64>(sides);
-    case 32: return bps_sides<32, 64>(sides);
-    case 48: return bps_sides<48, 32>(sides);
-    case 64: return bps_sides<64, 32>(sides);
+#define CPG_BPS(RT_, TJ, TJL) \
+  case RT_: return bps_sides<RT_, TJ, TJL>(sides);
+    CPG_F32_INSTANCES(CPG_BPS)
+#undef CPG_BPS
     default: return 1;
   }
 }
 
 cudaError_t launch_lead_f32(const LeadArgs<float>& a, int RT, int sides, dim3 grid, cudaStream_t st) {
   switch (RT) {
-    case 4: return run_sides<4, 256>(a, sides, grid, st);
-    case 8: return run_sides<8, 256>(a, sides, grid, st);
-    case 10: return run_sides<10, 128>(a, sides, grid, st);
-    case 12: return run_sides<12, 128>(a, sides, grid, st);
-    case 16: return run_sides<16, 128>(a, sides, grid, st);
-    case 24: return run_sides<24, 64>(a, sides, grid, st);
-    case 32: return run_sides<32, 64>(a, sides, grid, st);
-    case 48: return run_sides<48, 32>(a, sides, grid, st);
-    case 64: return run_sides<64, 32>(a, sides, grid, st);
+#define CPG_RUN(RT_, TJ, TJL) \
+  case RT_: return run_sides<RT_, TJ, TJL>(a, sides, grid, st);
+    CPG_F32_INSTANCES(CPG_RUN)
+#undef CPG_RUN
     default: return cudaErrorInvalidValue;
   }
 }

@@ -61,7 +61,7 @@ SimtShape shape() {
 }
 }  // namespace
 
-SimtShape simt_shape_f64(int r) {
+SimtShape simt_shape_f64(int r, int) {
   if (r <= 4) return shape<4, 128>();
   if (r <= 8) return shape<8, 128>();
   return shape<16, 64>();

@@ -230,9 +230,15 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   }
 
   // Stage `it` (column chunk it / nrt, row tile it % nrt) into buffer it % STAGES.
+  // Element copies commit one cp.async group per call, empty past the last
+  // stage, so that "all but STAGES - 2 groups complete" always means "stage
+  // it has landed".
   int issued = 0;  // stages issued so far
   auto issue = [&](int it) {
-    if (it >= nst) return;
+    if (it >= nst) {
+      if (!use_tma) cp_async_commit();
+      return;
+    }
     issued = it + 1;
     T* dst = Ys + size_t(it % STAGES) * TK * TJ;
     const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
