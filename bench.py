@@ -415,7 +415,7 @@ def main():
 
 LEAD_KERNELS = {
     # kernel family -> (sources whose hash identifies the captured build, traffic summary)
-    "lead_simt_kernel": (("lead_simt.cuh", "common.cuh"), "lead_simt_traffic.json"),
+    "lead_simt_kernel": (("lead_simt.cuh", "common.cuh", "tc_common.cuh"), "lead_simt_traffic.json"),
     "lead_tc_kernel": (("lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tc_traffic.json"),
 }
 

@@ -3,8 +3,9 @@
 //
 // For mode n, with the gradient G = Y_(n) KR from the chain kernels:
 //   V        = Hadamard_{m != n} Gram_m          (Gram_m = A^(m)T A^(m))
-//   V^{-1}   by Gauss-Jordan elimination of [V | I]
-//   X        = G V^{-1}
+//   V^{-1}   by Gauss-Jordan elimination of [V | I] (als_inverse_df_kernel,
+//            which needs only the Grams and so can run ahead of G)
+//   X        = G V^{-1}                          (als_update_df_kernel, below)
 //   lambda_q = ||x_q||,  a_q = x_q / lambda_q    (column normalisation)
 //   Gram_n   = A^(n)T A^(n) of the stored FP32 factor (products exact, sums compensated)
 // and after the last mode of a sweep the fit from R x R quantities:
@@ -34,6 +35,8 @@ struct AlsDfArgs {
   int N, n, R;
   int64_t In;
   df* grams;              // [N][R][R] double-float Grams
+  const df* Vi;           // [R][R] V^{-1} of this mode (from als_inverse_df_kernel)
+  const df* V;            // [R][R] V of this mode
   const float* G;         // In x R, column-major
   float* An;              // In x R, column-major (updated in place)
   double* lambda;         // [R]
@@ -55,68 +58,50 @@ __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
   grams[(int64_t(m) * R + b) * R + a] = s;
 }
 
-// Threads of the update block: enough for one Gauss-Jordan entry and about two
-// entries of X per thread at small ranks.
-inline int als_df_threads(int R) { return R <= 16 ? 512 : 1024; }
+// ---- V and V^{-1} of one mode ------------------------------------------------------
+constexpr int kInvThreads = 256;
 
-inline size_t als_df_smem_bytes(int64_t In, int R) {
-  const size_t RS = size_t(R) + 1;
-  // [V | I] (R x 2R), two column and two row buffers, lambda, 1/lambda, partials, X, the factor panel.
-  return (2 * size_t(R) * R + 2 * size_t(R) + 4 * size_t(R) + 3 * size_t(R)) * sizeof(df) +
-         size_t(In) * RS * (sizeof(df) + sizeof(float)) + 16;
-}
+inline size_t als_inv_smem_bytes(int R) { return (2 * size_t(R) * R + 2 * size_t(R) + 4 * size_t(R)) * sizeof(df); }
 
-__device__ __forceinline__ df df_warp_sum(df v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-  return v;
-}
-
-// One block of als_df_threads(R) threads.  Shared memory: als_df_smem_bytes(In, R).
-// Phases (each a short dependent chain, all entries in parallel):
-//   V^{-1}   R Gauss-Jordan steps on [V | I], one barrier each: step j
-//            scales row j by 1 / pivot and removes column j from the other
-//            rows, reading row j and column j from the side buffers written
-//            by step j - 1 (so every entry updates in place);
-//   X        = G V^{-1}, one output per thread;
-//   lambda   warp per column; Gram: 8 lanes per (p, q) pair.
-__global__ void __launch_bounds__(1024) als_update_df_kernel(const AlsDfArgs a) {
+// V = Hadamard_{m != n} Gram_m and V^{-1} by Gauss-Jordan elimination of
+// [V | I]; one block of kInvThreads threads, als_inv_smem_bytes(R) of shared
+// memory.  Writes V and V^{-1} ([R][R], symmetric); a pivot that is not
+// positive (V not positive definite) records CPG_ERR_SINGULAR and writes a
+// zero pivot marker (Vi[0] = 0) that the update kernel checks.
+// Step j of the elimination touches only the R columns j+1 .. R+j (earlier left
+// columns are finished unit vectors, later right columns are still identity
+// columns) and reads row j and column j from side buffers written by step
+// j - 1, so every entry updates in place with one barrier per step.
+__global__ void __launch_bounds__(kInvThreads) als_inverse_df_kernel(const df* grams, int N, int n, int R, df* V,
+                                                                      df* Vi, int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int R = a.R, N = a.N, n = a.n, RS = R + 1, R2 = 2 * R;
-  const int64_t In = a.In;
-  df* M = reinterpret_cast<df*>(smraw);      // [V | I], row-major: M[i * 2R + c]
-  df* colb = M + R * R2;                     // column j of M, two buffers of R
-  df* rowb = colb + 2 * R;                   // row j of M, two buffers of 2R
-  df* lam = rowb + 2 * R2;                   // lambda_q
-  df* ilam = lam + R;                        // 1 / lambda_q
-  df* part = ilam + R;                       // per-column partial inner products
-  df* X = part + R;                          // X[i*RS + q]
-  float* Af = reinterpret_cast<float*>(X + In * RS);  // G, then the stored factor: Af[i*RS + q]
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int R2 = 2 * R;
+  df* M = reinterpret_cast<df*>(smraw);  // [V | I], row-major: M[i * 2R + c]
+  df* colb = M + R * R2;                 // column j of M, two buffers of R
+  df* rowb = colb + 2 * R;               // row j of M, two buffers of 2R
+  const int tid = threadIdx.x, nt = blockDim.x;
 
-  for (int64_t t = tid; t < In * R; t += nt) {
-    const int q = int(t / In);
-    const int64_t i = t - int64_t(q) * In;
-    Af[i * RS + q] = a.G[t];
+  for (int t = tid; t < R * R; t += nt) {
+    df g[kMaxOrder];
+#pragma unroll
+    for (int m = 0; m < kMaxOrder; ++m)
+      if (m < N && m != n) g[m] = grams[m * R * R + t];  // every load in flight before the products
+    df v = df_make(1.f);
+#pragma unroll
+    for (int m = 0; m < kMaxOrder; ++m)
+      if (m < N && m != n) v = df_mul(v, g[m]);
+    const int i = t % R, c = t / R;  // V is symmetric: V[i][c]
+    V[t] = v;
+    M[i * R2 + c] = v;
+    M[i * R2 + R + c] = df_make(i == c ? 1.f : 0.f);
+    if (c == 0) colb[i] = v;  // column 0 for step 0
+    if (i == 0) rowb[c] = v;  // row 0, left half
   }
-  for (int e = tid; e < R * R2; e += nt) {
-    const int i = e / R2, c = e - i * R2;
-    df v;
-    if (c < R) {
-      v = df_make(1.f);
-      for (int m = 0; m < N; ++m)
-        if (m != n) v = df_mul(v, a.grams[int64_t(m) * R * R + i + R * c]);
-    } else {
-      v = df_make(c - R == i ? 1.f : 0.f);
-    }
-    M[e] = v;
-    if (c == 0) colb[i] = v;
-    if (i == 0) rowb[c] = v;
-  }
+  // Column R + j of row j still holds the identity's 1 when step j first
+  // touches it, and no earlier step writes that side-buffer slot: preset it.
+  for (int j = tid; j < R; j += nt) rowb[(j & 1) * R2 + R + j] = df_make(1.f);
   __syncthreads();
 
-  // Gauss-Jordan: after step j, columns <= j of the left half are unit
-  // vectors (never read again) and the right half holds the running inverse.
   bool fail = false;
   for (int j = 0; j < R; ++j) {
     const df* col = colb + (j & 1) * R;
@@ -129,74 +114,137 @@ __global__ void __launch_bounds__(1024) als_update_df_kernel(const AlsDfArgs a) 
       break;
     }
     const df inv = df_rcp(p);
-    for (int e = tid; e < R * R2; e += nt) {
-      const int i = e / R2, c = e - i * R2;
-      if (c <= j) continue;
-      const df v = (i == j) ? df_mul(row[c], inv) : df_sub(M[e], df_mul(df_mul(col[i], inv), row[c]));
-      M[e] = v;
+    for (int e = tid; e < R * R; e += nt) {
+      const int i = e / R, c = j + 1 + (e - i * R);
+      const df v = (i == j) ? df_mul(row[c], inv) : df_sub(M[i * R2 + c], df_mul(df_mul(col[i], inv), row[c]));
+      M[i * R2 + c] = v;
       if (c == j + 1) coln[i] = v;
       if (i == j + 1) rown[c] = v;
     }
     __syncthreads();
   }
   if (fail) {
-    if (tid == 0) atomicCAS(a.status, 0, int(CPG_ERR_SINGULAR));
+    if (tid == 0) {
+      atomicCAS(status, 0, int(CPG_ERR_SINGULAR));
+      Vi[0] = df{0.f, 0.f};
+    }
     return;
   }
+  for (int t = tid; t < R * R; t += nt) {
+    const int p = t % R, q = t / R;
+    Vi[t] = M[p * R2 + R + q];
+  }
+}
 
-  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], Vi[p, q] = M[p * 2R + R + q].
-  for (int64_t t = tid; t < In * R; t += nt) {
-    const int q = int(t / In);
-    const int64_t i = t - int64_t(q) * In;
-    const float* g = Af + i * RS;
-    const df* vi = M + R + q;
+// ---- the update of one mode given V^{-1} -------------------------------------------
+constexpr int kAlsThreads = 1024;
+
+inline size_t als_df_smem_bytes(int64_t In, int R) {
+  const size_t RS = size_t(R) + 1, R2 = size_t(R) * R;
+  // V^{-1}, V, Gram_n, lambda, partials; X (df), then G and the new factor
+  // (floats), all In x RS.
+  return (3 * R2 + 2 * size_t(R)) * sizeof(df) + size_t(In) * RS * (sizeof(df) + 2 * sizeof(float)) + 16;
+}
+
+__device__ __forceinline__ df df_warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
+}
+
+// One block of kAlsThreads threads.  Shared memory: als_df_smem_bytes(In, R).
+// Phases (each a short dependent chain, all entries in parallel):
+//   load     G, V^{-1}, V;
+//   X        = G V^{-1}, one output per thread;
+//   lambda   warp per column; a_q = x_q / lambda_q;
+//   Gram_n   8 lanes per (p, q) pair;
+//   fit      <Y, Yhat> = sum_q lambda_q <a_q, g_q>,
+//            ||Yhat||^2 = lambda^T (V * Gram_n) lambda.
+__global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int R = a.R, n = a.n, RS = R + 1;
+  const int In = int(a.In);  // In * (R + 1) fits the shared-memory budget, far below 2^31
+  df* Vis = reinterpret_cast<df*>(smraw);    // V^{-1}[p][q] at p + R q
+  df* Vs = Vis + R * R;                      // V
+  df* gn = Vs + R * R;                       // Gram_n of the new factor
+  df* lam = gn + R * R;                      // lambda_q
+  df* part = lam + R;                        // lambda_q <a_q, g_q>
+  df* X = part + R;                          // X[i*RS + q]
+  float* Gs = reinterpret_cast<float*>(X + In * RS);  // G[i*RS + p]
+  float* Fs = Gs + In * RS;                            // new factor[i*RS + q]
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const bool want_fit = a.fit_out != nullptr;
+
+  if (!(a.Vi[0].hi != 0.f)) return;  // V was not positive definite: leave this mode untouched
+  for (int t = tid; t < In * R; t += nt) {
+    const int q = t / In, i = t - q * In;
+    Gs[i * RS + q] = a.G[t];
+  }
+  for (int t = tid; t < R * R; t += nt) {
+    Vis[t] = a.Vi[t];
+    Vs[t] = a.V[t];
+  }
+  __syncthreads();
+
+  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], one output per thread.
+  for (int t = tid; t < In * R; t += nt) {
+    const int q = t / In, i = t - q * In;
+    const float* g = Gs + i * RS;
+    const df* vi = Vis + R * q;
     df s0{0.f, 0.f}, s1{0.f, 0.f};
     int p = 0;
     for (; p + 1 < R; p += 2) {
-      s0 = df_add(s0, df_mul_f(vi[p * R2], g[p]));
-      s1 = df_add(s1, df_mul_f(vi[(p + 1) * R2], g[p + 1]));
+      s0 = df_add(s0, df_mul_f(vi[p], g[p]));
+      s1 = df_add(s1, df_mul_f(vi[p + 1], g[p + 1]));
     }
-    if (p < R) s0 = df_add(s0, df_mul_f(vi[p * R2], g[p]));
+    if (p < R) s0 = df_add(s0, df_mul_f(vi[p], g[p]));
     X[i * RS + q] = df_add(s0, s1);
   }
   __syncthreads();
 
-  // lambda_q = ||x_q||, 1/lambda_q = rsqrt(||x_q||^2).
+  // lambda_q = ||x_q||, a_q = x_q / lambda_q (1/lambda_q = rsqrt(||x_q||^2)), warp per column.
   for (int q = warp; q < R; q += nw) {
-    df s{0.f, 0.f};
-    for (int64_t i = lane; i < In; i += 32) s = df_add(s, df_mul(X[i * RS + q], X[i * RS + q]));
-    s = df_warp_sum(s);
-    if (lane == 0) {
-      if (s.hi > 0.f) {
-        const df rs = df_rsqrt(s);
-        lam[q] = df_mul(s, rs);
-        ilam[q] = rs;
-      } else {
-        lam[q] = df{0.f, 0.f};
-        ilam[q] = df_make(1.f);
-      }
-      a.lambda[q] = df_to_double(lam[q]);
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
+    int i = lane;
+    for (; i + 32 < In; i += 64) {
+      s0 = df_add(s0, df_mul(X[i * RS + q], X[i * RS + q]));
+      s1 = df_add(s1, df_mul(X[(i + 32) * RS + q], X[(i + 32) * RS + q]));
     }
-  }
-  __syncthreads();
-  for (int64_t t = tid; t < In * R; t += nt) {
-    const int q = int(t / In);
-    const int64_t i = t - int64_t(q) * In;
-    const df v = df_mul(X[i * RS + q], ilam[q]);
-    const float f = __fadd_rn(v.hi, v.lo);
-    a.An[t] = f;
-    Af[i * RS + q] = f;
+    if (i < In) s0 = df_add(s0, df_mul(X[i * RS + q], X[i * RS + q]));
+    const df ss = df_warp_sum(df_add(s0, s1));
+    df lq, il;
+    if (ss.hi > 0.f) {
+      il = df_rsqrt(ss);
+      lq = df_mul(ss, il);
+    } else {
+      lq = df{0.f, 0.f};
+      il = df_make(1.f);
+    }
+    df ip{0.f, 0.f};
+    for (int r = lane; r < In; r += 32) {
+      const df v = df_mul(X[r * RS + q], il);
+      const float f = __fadd_rn(v.hi, v.lo);
+      a.An[r + In * q] = f;
+      Fs[r * RS + q] = f;
+      if (want_fit) ip = df_add_prod_ff(ip, f, Gs[r * RS + q]);
+    }
+    if (want_fit) ip = df_warp_sum(ip);
+    if (lane == 0) {
+      lam[q] = lq;
+      part[q] = df_mul(lq, ip);
+      a.lambda[q] = df_to_double(lq);
+    }
   }
   __syncthreads();
 
   // Gram of the stored factor: 8 lanes per (p <= q) pair.
-  df* gn = a.grams + int64_t(n) * R * R;
+  df* gout = a.grams + int64_t(n) * R * R;
   const int npairs = R * (R + 1) / 2;
   const int sub = tid & 7, ngroups = nt >> 3;
   for (int pq0 = 0; pq0 < npairs; pq0 += ngroups) {
     const int pq = pq0 + (tid >> 3);
     int p = 0, q = 0;
-    df s{0.f, 0.f};
+    df s0{0.f, 0.f}, s1{0.f, 0.f};
     if (pq < npairs) {
       int rem = pq;
       while (rem >= R - p) {
@@ -204,32 +252,31 @@ __global__ void __launch_bounds__(1024) als_update_df_kernel(const AlsDfArgs a) 
         ++p;
       }
       q = p + rem;
-      for (int64_t i = sub; i < In; i += 8) s = df_add_prod_ff(s, Af[i * RS + p], Af[i * RS + q]);
+      int i = sub;
+      for (; i + 8 < In; i += 16) {
+        s0 = df_add_prod_ff(s0, Fs[i * RS + p], Fs[i * RS + q]);
+        s1 = df_add_prod_ff(s1, Fs[(i + 8) * RS + p], Fs[(i + 8) * RS + q]);
+      }
+      if (i < In) s0 = df_add_prod_ff(s0, Fs[i * RS + p], Fs[i * RS + q]);
     }
+    df s = df_add(s0, s1);
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o, 8));
     if (pq < npairs && sub == 0) {
+      gout[p + R * q] = s;
+      gout[q + R * p] = s;
       gn[p + R * q] = s;
       gn[q + R * p] = s;
     }
   }
-  if (a.fit_out == nullptr) return;
+  if (!want_fit) return;
   __syncthreads();
-  for (int q = warp; q < R; q += nw) {
-    df s{0.f, 0.f};
-    for (int64_t i = lane; i < In; i += 32) s = df_add_prod_ff(s, Af[i * RS + q], a.G[i + In * q]);
-    s = df_warp_sum(s);
-    if (lane == 0) part[q] = df_mul(lam[q], s);
-  }
-  __syncthreads();
+
   if (warp == 0) {
     df inner{0.f, 0.f}, model{0.f, 0.f};
     for (int q = lane; q < R; q += 32) inner = df_add(inner, part[q]);
-    for (int t = lane; t < R * R; t += 32) {
-      df v = df_mul(lam[t % R], lam[t / R]);
-      for (int m = 0; m < N; ++m) v = df_mul(v, a.grams[int64_t(m) * R * R + t]);
-      model = df_add(model, v);
-    }
+    for (int t = lane; t < R * R; t += 32)
+      model = df_add(model, df_mul(df_mul(lam[t % R], lam[t / R]), df_mul(Vs[t], gn[t])));
     inner = df_warp_sum(inner);
     model = df_warp_sum(model);
     if (lane == 0) {

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -374,6 +375,8 @@ struct AlsWs {
   double* X;
   T* G;
   LeadTabs<T> tabs;
+  double* Vinv;  // [N][R][R] V^{-1} per mode (double-float pairs for FP32 data)
+  double* Vm;    // [N][R][R] V per mode
 };
 
 template <typename T>
@@ -391,8 +394,36 @@ AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const 
   w.X = c.take<double>(size_t(imax) * R);
   w.G = c.take<T>(size_t(imax) * R);
   w.tabs = take_tabs<T>(c, s, R, lr.k);
+  w.Vinv = c.take<double>(size_t(s.N) * R * R);
+  w.Vm = c.take<double>(size_t(s.N) * R * R);
   if (bytes) *bytes = c.off;
   return w;
+}
+
+// A second stream per device for work that depends only on small R x R
+// quantities (the normal-equation inverses of fast CP_ALS), so that it runs
+// while the main stream streams Y or contracts partial sums; ordered with the
+// main stream by events only.  Created once per device and kept.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;                // main -> side
+  cudaEvent_t done[kMaxOrder] = {};          // side -> main, one per mode
+};
+
+SideStream* side_stream() {
+  static SideStream table[64];
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  SideStream& ss = table[dev];
+  if (ss.stream == nullptr) {
+    if (cudaStreamCreateWithFlags(&ss.stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (auto& e : ss.done)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  }
+  return &ss;
 }
 
 inline int blocks_for(int64_t n, int threads, int cap = 4 * 1024) {
@@ -715,10 +746,15 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   for (int m = 0; m < s.N; ++m) imax = std::max(imax, s.I[m]);
   constexpr size_t kSmemCap = 200 * 1024;
   const bool smem_path = (kDf ? als_df_smem_bytes(imax, R) : als_smem_bytes(imax, R)) <= kSmemCap;
+  SideStream* side = nullptr;
   if constexpr (kDf) {
     if (!smem_path) return CPG_ERR_UNSUPPORTED;
     cudaFuncSetAttribute(als_update_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(als_df_smem_bytes(imax, R)));
+    cudaFuncSetAttribute(als_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(als_inv_smem_bytes(R)));
+    side = side_stream();
+    if (side == nullptr) return CPG_ERR_CUDA;
   } else {
     cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
     if (smem_path)
@@ -736,6 +772,29 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     launch_grad<T, RIGHT>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
     return w.G;
   };
+  // Update order of one sweep (Section 4): k-1, ..., 0, then k, ..., N-1.
+  std::vector<int> order;
+  for (int m = k - 1; m >= 0; --m) order.push_back(m);
+  for (int m = k; m < s.N; ++m) order.push_back(m);
+  const int64_t total_updates = int64_t(iters) * s.N;
+  int64_t upd = 0;  // updates issued so far
+  df* const Vi_all = reinterpret_cast<df*>(w.Vinv);
+  df* const V_all = reinterpret_cast<df*>(w.Vm);
+  // V and V^{-1} of mode n on the side stream, after everything issued so far
+  // on the main stream (the Grams it reads are then final).
+  auto fork_inverse = [&](int n) {
+    if constexpr (kDf) {
+      cudaEventRecord(side->fork, st);
+      cudaStreamWaitEvent(side->stream, side->fork, 0);
+      ++g_launches;
+      als_inverse_df_kernel<<<1, kInvThreads, als_inv_smem_bytes(R), side->stream>>>(
+          reinterpret_cast<const df*>(w.grams), s.N, n, R, V_all + int64_t(n) * R * R, Vi_all + int64_t(n) * R * R,
+          w.h.status);
+      cudaEventRecord(side->done[n], side->stream);
+    }
+  };
+  if constexpr (kDf) fork_inverse(order[0]);
+
   auto update = [&](int n, const T* Gn, double* fit_out) {
     ++g_launches;
     if constexpr (kDf) {
@@ -745,13 +804,18 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.R = R;
       u.In = s.I[n];
       u.grams = reinterpret_cast<df*>(w.grams);
+      u.Vi = Vi_all + int64_t(n) * R * R;
+      u.V = V_all + int64_t(n) * R * R;
       u.G = Gn;
       u.An = static_cast<float*>(A[n]);
       u.lambda = lambda;
       u.status = w.h.status;
       u.fit_out = fit_out;
       u.normY2 = w.h.normY2;
-      als_update_df_kernel<<<1, als_df_threads(R), als_df_smem_bytes(s.I[n], R), st>>>(u);
+      cudaStreamWaitEvent(st, side->done[n], 0);
+      als_update_df_kernel<<<1, kAlsThreads, als_df_smem_bytes(s.I[n], R), st>>>(u);
+      // The next update's inverse needs this mode's new Gram: fork it now.
+      if (++upd < total_updates) fork_inverse(order[upd % s.N]);
     } else {
       AlsArgs<T> u{};
       u.N = s.N;

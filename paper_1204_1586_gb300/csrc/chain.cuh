@@ -57,7 +57,10 @@ struct SegDot {
   int R;
 };
 
-// LPO lanes cooperate on one output; lanes stride the reduction index.
+// LPO lanes cooperate on one output; lanes stride the reduction index.  The
+// partial sums of an element are loaded in batches of 8 ahead of their
+// additions (which keep the fixed order q = 0, 1, ...), so that the loads
+// overlap instead of each waiting for the previous add.
 template <typename T, int LPO>
 __global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
   const int64_t gid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -65,17 +68,33 @@ __global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
   const int sub = int(gid % LPO);
   const int64_t nout = p.D * p.R;
   const bool live = t < nout;
+  const T* __restrict__ X = p.X;
+  T* __restrict__ Xred = p.Xred;
+  const int nparts = p.nparts;
+  const int64_t pstride = p.part_stride;
   T acc = T(0);
   if (live) {
     const int r = int(t / p.D);
     const int64_t a = t - int64_t(r) * p.D;
     const int64_t base = int64_t(r) * p.S + a * p.astep;
-    const T* w = p.w ? p.w + int64_t(r) * p.wlen : nullptr;
+    const T* __restrict__ w = p.w ? p.w + int64_t(r) * p.wlen : nullptr;
+#pragma unroll 2
     for (int64_t u = sub; u < p.inner; u += LPO) {
       const int64_t off = base + u * p.ustep;
-      T x = p.X[off];
-      for (int q = 1; q < p.nparts; ++q) x += p.X[int64_t(q) * p.part_stride + off];
-      if (p.Xred) p.Xred[off] = x;
+      T x;
+      if (nparts == 1) {
+        x = X[off];
+      } else {
+        x = T(0);
+        for (int q0 = 0; q0 < nparts; q0 += 8) {
+          T v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = (q0 + e < nparts) ? X[(q0 + e) * pstride + off] : T(0);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x += v[e];
+        }
+        if (Xred) Xred[off] = x;
+      }
       acc = w ? fma(x, w[u], acc) : acc + x;
     }
   }
