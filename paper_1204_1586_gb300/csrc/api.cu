@@ -193,20 +193,55 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   p.TJ = 128;
   p.TK = 128;
   const int64_t tiles = (p.J + 127) / 128;
-  const int cap = std::min(tc_max_nrt(p.RTP, sides, p.tc_prec), sides == 2 ? 16 : 8);
-  p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
-  p.nJb = int((p.J + 128LL * p.nrt - 1) / (128LL * p.nrt));
-  choose_ksplit(p, num_sms());
+  if (sides == 2) {
+    // Step 7 alone: row tiles outer, one tensor-memory accumulator per column
+    // chunk (at most 512 / NW chunks per CTA), W_L built once per row tile.
+    // Minimise waves * (super-stages + W_L builds + fixed cost) + partial-sum
+    // traffic, as choose_grid does for the CUDA-core kernel (1 CTA per SM).
+    const int nw = p.tc_prec == 0 ? 2 * p.RTP : p.RTP;
+    const int64_t max_per = std::max(1, 512 / nw);
+    const int64_t chunks = (p.K + 127) / 128;
+    const int slots = num_sms();
+    const double wbuild = 0.25 * p.RTP / 16.0;  // one W_L build, in super-stages
+    double best = 1e300;
+    int64_t best_nrt = 1, best_per = 1;
+    std::vector<int64_t> nrts;
+    for (int64_t d = 1; d <= tiles;) {
+      const int64_t q = (tiles + d - 1) / d;
+      nrts.push_back(q);
+      d = (q > 1) ? (tiles + q - 2) / (q - 1) : tiles + 1;
+    }
+    for (int64_t nrt : nrts)
+      for (int64_t per = 1; per <= std::min(max_per, chunks); ++per) {
+        const int64_t nJb = (tiles + nrt - 1) / nrt, nCb = (chunks + per - 1) / per;
+        if (nJb > 65535 || nCb > 65535) continue;
+        const double waves = double((nJb * nCb + slots - 1) / slots);
+        const double partial = 2.0 * double(nJb) * R * double(p.K) * 4.0;
+        const double cost = waves * (double(per * nrt) + double(nrt) * wbuild + 2.0) + partial / (double(slots) * 65536.0);
+        if (cost < best - 1e-9) {
+          best = cost;
+          best_nrt = nrt;
+          best_per = per;
+        }
+      }
+    p.nrt = int(best_nrt);
+    p.nJb = int((tiles + best_nrt - 1) / best_nrt);
+    p.nKs = int((chunks + best_per - 1) / best_per);
+    p.Kc = best_per * 128;
+  } else {
+    const int cap = std::min(tc_max_nrt(p.RTP, sides, p.tc_prec), 8);
+    p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
+    p.nJb = int((p.J + 128LL * p.nrt - 1) / (128LL * p.nrt));
+    choose_ksplit(p, num_sms());
+  }
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
   p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
   return p;
 }
 
 LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
-  // Split-BF16 forms run on the tensor cores when rows are whole 16-byte
-  // chunks (a TMA requirement); otherwise the FP32 CUDA-core kernel runs.
-  if (is_tc_prec(prec) && (prod(s, 0, k) % 4) == 0) return plan_lead_tc(s, R, k, sides, prec);
-  if (is_tc_prec(prec)) prec = CPG_FP32;
+  // Split-BF16 forms run on the tensor cores.
+  if (is_tc_prec(prec)) return plan_lead_tc(s, R, k, sides, prec);
   LeadPlan p;
   p.k = k;
   p.sides = sides;
@@ -632,7 +667,6 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
   if (!lead_fits(pr) || !lead_fits(pl)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
-  if ((pr.tc || pl.tc) && !tc_eligible(reinterpret_cast<const float*>(Y), pr.J)) return CPG_ERR_UNSUPPORTED;
   g_status_ptr = w.h.status;
 
   // Steps 4 and 7: R^(k) and L^(k+1) from one read of Y (or two passes).
@@ -698,7 +732,6 @@ cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, 
   ModeWs<T> w = carve_mode<T>(o->workspace, s, R, n, rt, &need);
   if (!lead_fits(rt.lead)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
-  if (rt.lead.tc && !tc_eligible(reinterpret_cast<const float*>(Y), rt.lead.J)) return CPG_ERR_UNSUPPORTED;
   g_status_ptr = w.h.status;
   const LeadPlan& p = rt.lead;
   if (rt.right) {
@@ -730,7 +763,6 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
   if (!lead_fits(lr) || !lead_fits(ll)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
-  if ((lr.tc || ll.tc) && !tc_eligible(reinterpret_cast<const float*>(Y), lr.J)) return CPG_ERR_UNSUPPORTED;
   g_status_ptr = w.h.status;
   const void* const* Ac = const_cast<const void* const*>(A);
 

@@ -44,21 +44,19 @@ int tc_rank_tile(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 
 int tc_max_nrt(int RTP, int sides, int prec) {
   const int nw = (prec == 0) ? 2 * RTP : RTP;
-  if (sides == 2) return 1 << 20;     // only the step-7 accumulators live in tensor memory
+  if (sides == 2) return 1 << 20;     // row tiles are outer: any number per CTA
   return sides == 1 ? 512 / nw : 512 / nw - 2;  // fused: two step-7 accumulators
 }
 
-bool tc_eligible(const float* Y, int64_t J) {
-  return (reinterpret_cast<uintptr_t>(Y) % 16) == 0 && (J % 4) == 0 && tensor_map_encoder() != nullptr;
-}
-
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {
-  CUtensorMap m;
-  if (!make_y_map(&m, Y, a.J, a.K)) return cudaErrorInvalidValue;
+  CUtensorMap m{};
+  TcArgs b = a;
+  b.Y = Y;
+  b.use_tma = make_y_map(&m, Y, a.J, a.K) ? 1 : 0;  // else element copies (rows not 16-byte aligned)
   switch (RTP) {
-    case 16: return run_prec<16>(m, a, sides, prec, grid, st);
-    case 32: return run_prec<32>(m, a, sides, prec, grid, st);
-    case 64: return run_prec<64>(m, a, sides, prec, grid, st);
+    case 16: return run_prec<16>(m, b, sides, prec, grid, st);
+    case 32: return run_prec<32>(m, b, sides, prec, grid, st);
+    case 64: return run_prec<64>(m, b, sides, prec, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -52,6 +52,8 @@ struct TcArgs {
   float* Lpart;    // [nJb][R][K]
   double* normpart;  // [nJb*nKs] partial sums of y^2 (R side only), or nullptr
   int* status;
+  const float* Y;  // the tensor (element copies when use_tma == 0)
+  int use_tma;     // 1: TMA boxes; 0: every thread copies elements (rows not 16-byte aligned)
 };
 
 template <int RTP, int SIDES, int PREC>
@@ -112,6 +114,13 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo
   hi.w = split2(x[6], x[7], lo.w);
 }
 
+// 4-byte copy global -> shared with zero fill (src_bytes = 0 writes zeros and
+// reads nothing).
+__device__ __forceinline__ void cp_async_zfill4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tc::smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
 template <int RTP, int SIDES, int PREC>
 __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs a) {
   using C = TcCfg<RTP, SIDES, PREC>;
@@ -136,14 +145,21 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   const int64_t kend = (kbeg + a.Kc < K) ? (kbeg + a.Kc) : K;
   const int nchunk = int((kend - kbeg + 127) / 128);
   const int nss = nchunk * nrt;
-  const int tcols_needed = (DO_R ? nrt : 0) * C::NW + (DO_L ? 2 * C::NW : 0);
+  // Step 7 alone walks row tiles in the outer loop and keeps one accumulator
+  // per column chunk in tensor memory (the mirror of step 4, which keeps one
+  // per row tile): W_L is then built once per row tile, not per super-stage.
+  constexpr bool LOUT = SIDES == 2;
+  const int tcols_needed = LOUT ? nchunk * C::NW : (DO_R ? nrt : 0) * C::NW + (DO_L ? 2 * C::NW : 0);
   uint32_t tcols = 32;
   while (tcols < uint32_t(tcols_needed)) tcols <<= 1;
   const uint32_t colL0 = (DO_R ? nrt : 0) * C::NW;
 
+  const bool use_tma = a.use_tma != 0;
   if (tid == 0) {
     for (int b = 0; b < C::NB; ++b) {
-      tc::mbar_init(&bar_full[b], 1);
+      // TMA: one arrival with the byte count; element copies: one arrival per
+      // thread when its copies have landed.
+      tc::mbar_init(&bar_full[b], use_tma ? 1 : NT);
       tc::mbar_init(&bar_mma[b], 1);
     }
     tc::mbar_fence_init();
@@ -157,19 +173,45 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
 
   int last_issued = 0;  // super-stages whose TMA thread 0 has issued
   int mma_issued = 0;   // super-stages whose MMAs thread 0 has issued
+  // Super-stage ss -> (column chunk, row tile).
+  auto chunk_of = [&](int ss) { return LOUT ? ss % nchunk : ss / nrt; };
+  auto tile_of = [&](int ss) { return LOUT ? ss / nchunk : ss % nrt; };
   auto issue_tma = [&](int ss) {  // thread 0 only
     last_issued = ss + 1;
     const int b = ss % C::NB;
-    const int64_t cb = kbeg + int64_t(ss / nrt) * 128;
-    const int64_t j0 = jblk + int64_t(ss % nrt) * 128;
+    const int64_t cb = kbeg + int64_t(chunk_of(ss)) * 128;
+    const int64_t j0 = jblk + int64_t(tile_of(ss)) * 128;
     uint64_t* bar = &bar_full[b];
     tc::mbar_arrive_expect_tx(bar, C::BUF_BYTES);
     for (int h = 0; h < 2; ++h)
       tc::tma_load_2d(sm + C::OFF_BUF + b * C::BUF_BYTES + h * C::HALF, &tmap, int(j0), int(cb + 64 * h), bar);
   };
-  if (tid == 0) {
-    for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue_tma(ss);
-  }
+  // The same tile by element copies (every thread), in the TMA boxes' layout:
+  // column c at (c / 64) * HALF + (c % 64) * 512 bytes, rows contiguous;
+  // entries outside Y are zero-filled.
+  auto issue_copies = [&](int ss) {
+    last_issued = ss + 1;
+    const int b = ss % C::NB;
+    const int64_t cb = kbeg + int64_t(chunk_of(ss)) * 128;
+    const int64_t j0 = jblk + int64_t(tile_of(ss)) * 128;
+    unsigned char* dst = sm + C::OFF_BUF + b * C::BUF_BYTES;
+#pragma unroll 4
+    for (int f = tid; f < 128 * 128; f += NT) {
+      const int c = f >> 7, j = f & 127;
+      const int64_t cg = cb + c, jg = j0 + j;
+      const bool in = cg < K && jg < J;
+      cp_async_zfill4(dst + (c >> 6) * C::HALF + (c & 63) * 512 + j * 4, in ? a.Y + jg + J * cg : a.Y, in ? 4 : 0);
+    }
+    tc::cp_async_mbar_arrive(&bar_full[b]);
+  };
+  auto issue = [&](int ss) {
+    if (use_tma) {
+      if (tid == 0) issue_tma(ss);
+    } else {
+      issue_copies(ss);
+    }
+  };
+  for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue(ss);
 
   // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).  Lanes
   // take consecutive index pairs of one rank, so factor loads coalesce and
@@ -188,9 +230,10 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   };
 
   // L epilogue: D_L rows are the chunk's 128 columns.
+  auto dl_col = [&](int q) { return colL0 + uint32_t(LOUT ? q : (q & 1)) * C::NW; };
   auto epilogue_L = [&](int q) {
     if (warp < 4) {
-      const uint32_t col = colL0 + uint32_t(q & 1) * C::NW;
+      const uint32_t col = dl_col(q);
       const int64_t c = kbeg + int64_t(q) * 128 + 32 * warp + lane;
       float v[16], u[16];
 #pragma unroll
@@ -211,7 +254,7 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
   float ysq = 0.f;  // this thread's share of sum y^2 (rows beyond J are zero)
   bool ok = true;
   for (int ss = 0; ss < nss; ++ss) {
-    const int q = ss / nrt, rt = ss % nrt, b = ss % C::NB;
+    const int q = chunk_of(ss), rt = tile_of(ss), b = ss % C::NB;
     if (!tc::mbar_wait(&bar_full[b], uint32_t(ss / C::NB) & 1u)) ok = false;
     if (C::WB == 1 && ss > 0) {  // single W tiles: MMA(ss - 1) must be done before they are rewritten
       if (!tc::mbar_wait(&bar_mma[(ss - 1) % C::NB], uint32_t((ss - 1) / C::NB) & 1u)) ok = false;
@@ -258,14 +301,15 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
     // 3. Khatri-Rao tiles of this super-stage.
     const int64_t j0 = jblk + int64_t(rt) * 128;
     // W_R depends on the column chunk only (buffer q % WB, rebuilt at its first
-    // row tile); W_L on the row tile (buffer ss % WB).  The buffer being
+    // row tile); W_L on the row tile (buffer rt % WB at the first chunk of the
+    // row tile when rows are outer, else buffer ss % WB).  The buffer being
     // rebuilt was last read by MMAs that have completed.
-    const int wbr = q % C::WB, wbl = ss % C::WB;
+    const int wbr = q % C::WB, wbl = LOUT ? rt % C::WB : ss % C::WB;
     if constexpr (DO_R) {
       if (rt == 0) gen_w(sm + C::OFF_WR + wbr * C::W_BYTES, a.wr, cb, kend);
     }
     if constexpr (DO_L) {
-      if (nrt > 1 || ss == 0 || C::WB == 1) gen_w(sm + C::OFF_WL + wbl * C::W_BYTES, a.wl, j0, J);
+      if (LOUT ? q == 0 : (nrt > 1 || ss == 0 || C::WB == 1)) gen_w(sm + C::OFF_WL + wbl * C::W_BYTES, a.wl, j0, J);
     }
     tc::fence_async_smem();
     tc::tc_fence_before();
@@ -286,8 +330,8 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
         }
       }
       if constexpr (DO_L) {
-        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + (nrt > 1 || C::WB == 1 ? wbl : 0) * C::W_BYTES);
-        const uint32_t d = tbase + colL0 + uint32_t(q & 1) * C::NW;
+        const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + (LOUT || nrt > 1 || C::WB == 1 ? wbl : 0) * C::W_BYTES);
+        const uint32_t d = tbase + dl_col(q);
         for (int s = 0; s < 8; ++s) {
           const uint32_t koff = (s >> 2) * 1024 + (s & 3) * 32;
           const uint64_t bd = tc::smem_desc_sw128(w0 + koff, 16, 2048);
@@ -306,10 +350,10 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
       const int p = ss - 1;
       if (!tc::mbar_wait(&bar_mma[p % C::NB], uint32_t(p / C::NB) & 1u)) atomicExch(&abort_flag, 1);
       tc::tc_fence_after();
-      if constexpr (DO_L) {
+      if constexpr (DO_L && !LOUT) {
         if (p % nrt == nrt - 1 && !abort_flag) epilogue_L(p / nrt);
       }
-      if (tid == 0 && p + C::NB < nss && !abort_flag) issue_tma(p + C::NB);
+      if (p + C::NB < nss && !abort_flag) issue(p + C::NB);
     }
   }
 
@@ -321,7 +365,11 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
     __syncthreads();
     aborted = abort_flag != 0;
     if (!aborted) {
-      if constexpr (DO_L) epilogue_L(nchunk - 1);
+      if constexpr (LOUT) {
+        for (int q = 0; q < nchunk; ++q) epilogue_L(q);
+      } else if constexpr (DO_L) {
+        epilogue_L(nchunk - 1);
+      }
       if constexpr (DO_R) {
         if (warp < 4) {
           for (int rt = 0; rt < nrt; ++rt) {

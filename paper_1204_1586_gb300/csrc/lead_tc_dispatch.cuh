@@ -13,7 +13,6 @@ int tc_rank_tile(int r);
 // tensor memory (no limit for a single side).
 int tc_max_nrt(int RTP, int sides, int prec);
 // TMA needs a 16-byte aligned tensor and rows of whole 16-byte chunks.
-bool tc_eligible(const float* Y, int64_t J);
 // prec: 0 = BF16x3 split product, 1 = single BF16 product.
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st);
 

@@ -43,6 +43,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// Arrives on `bar` (without raising its expected count) once all cp.async
+// copies this thread issued before have landed.
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // ---- proxies -------------------------------------------------------------------
 // Generic-proxy shared-memory writes made visible to the async proxy (tensor
 // core operand reads, TMA).

@@ -62,13 +62,16 @@ GRAD_CASES = [
     ([13, 7, 9, 11], 8, "fp64"),
     ([21, 22, 23], 16, "fp64"),
     ([5, 6, 7], 20, "fp64"),            # two rank groups in FP64
-    # split-BF16 forms on the tensor cores (J * 4 a multiple of 16)
+    # split-BF16 forms on the tensor cores (TMA boxes when J * 4 is a multiple
+    # of 16, element copies otherwise)
     ([24, 20, 30, 17], 12, "bf16x3"),   # k=2, J=480: ragged row tile and column chunk
     ([100, 100, 100], 20, "bf16x3"),    # k=1, J=100, rank tile 32
     ([64, 64, 64, 4], 3, "bf16x3"),
     ([32, 16, 20, 24, 10], 10, "bf16x3"),
     ([12, 11, 10, 9], 64, "bf16x3"),    # rank tile 64 (J=132)
-    ([9, 10, 11], 70, "bf16x3"),        # J=9: rows not 16-byte multiples -> FP32 CUDA-core path
+    ([9, 10, 11], 70, "bf16x3"),        # J=9: element copies, two rank groups
+    ([15, 15, 15, 15, 15], 10, "bf16x3"),  # J=225: element copies
+    ([7, 9, 11, 13], 20, "bf16"),       # J=63: element copies, pure BF16
     ([20, 12, 40, 36], 33, "bf16x3"),   # rank tile 64, R not a multiple of 16
     ([40, 36, 28, 20], 16, "bf16"),
     ([100, 100, 100], 10, "bf16"),
@@ -138,6 +141,24 @@ def test_gradient_deterministic(cg):
     torch.cuda.synchronize()
     for a, b in zip(G1, G2):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("R", [10, 20])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_precision_study_7d(cg, R, prec):
+    """The 7-D collinear workload's recipe (factor columns with pairwise
+    cosine 0.5, 30 dB noise) at I = 7 per mode: per-mode relative Frobenius
+    error of every precision against the FP64 oracle.  J = 343 rows per
+    column are not 16-byte multiples, so the tensor-core forms take the
+    element-copy path."""
+    p = cpsynth.make_problem([7] * 7, R, snr_db=30.0, seed=7, dtype=np.float32, collinearity=0.5)
+    Y = torch.from_numpy(p.y).cuda()
+    Ad = [dev_factor(a, np.float32) for a in p.factors]
+    G = cg.cp_gradient_all(Y, p.I, Ad, precision=prec)
+    torch.cuda.synchronize()
+    want = oracle.cp_gradient_all(p.y.astype(np.float64), p.I, p.factors)
+    errs = [rel(G[n].double().cpu().numpy(), want[n]) for n in range(7)]
+    assert max(errs) <= TOL[prec], errs
 
 
 @pytest.mark.slow
