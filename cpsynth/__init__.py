@@ -155,3 +155,19 @@ WORKLOADS = {
 def workload(name: str, seed: int = DEFAULT_SEED) -> Problem:
     I, R, snr, dt, col, _ = WORKLOADS[name]
     return make_problem(I, R, snr_db=snr, seed=seed, dtype=dt, collinearity=col)
+
+
+def batched_workload(count: int = 256, seed: int = DEFAULT_SEED, orders=(3, 4, 5), size_range=(8, 64),
+                     rank_range=(4, 32), snr_db: float = 20.0, dtype=np.float32) -> list[Problem]:
+    """Many independent CP problems from one seed: order N uniform in
+    `orders`, every I_n uniform in `size_range` (inclusive), rank R uniform in
+    `rank_range` (inclusive), each a rank-R N(0,1) CP model plus Gaussian noise
+    at `snr_db`, with its own seeded ALS start."""
+    g = rng(seed, 77)
+    probs = []
+    for b in range(count):
+        N = int(g.choice(orders))
+        I = [int(v) for v in g.integers(size_range[0], size_range[1] + 1, size=N)]
+        R = int(g.integers(rank_range[0], rank_range[1] + 1))
+        probs.append(make_problem(I, R, snr_db=snr_db, seed=seed + 1 + b, dtype=dtype))
+    return probs

@@ -112,9 +112,10 @@ cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* 
 
 /* `iters` sweeps of the fast CP_ALS of Section 4 with update rule eq. 2.14.
  * Mode order per sweep (0-based, k = split): k-1, k-2, ..., 0, k, ..., N-1.
- * Each update solves A^(n) V = G^(n), V = Hadamard_{m != n} A^(m)T A^(m), by
- * FP64 Cholesky, then normalises the columns: lambda_r = ||a_r^(n)||,
- * a_r^(n) /= lambda_r.  A[n] (device, I_n x R) and lambda (device, R
+ * Each update solves A^(n) V = G^(n), V = Hadamard_{m != n} A^(m)T A^(m)
+ * (Gauss-Jordan inverse of V in double-float arithmetic for FP32 data, FP64
+ * Cholesky for FP64 data), then normalises the columns: lambda_r =
+ * ||a_r^(n)||, a_r^(n) /= lambda_r.  R <= 64.  A[n] (device, I_n x R) and lambda (device, R
  * doubles) are updated in place; A on entry is the starting point.
  * fit (device, `iters` doubles, may be NULL) receives after each sweep
  * fit = 1 - ||Y - Yhat||_F / ||Y||_F computed from R x R quantities.
@@ -122,6 +123,40 @@ cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* 
  * CPG_ERR_SINGULAR in the device status word. */
 cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
                        int iters, double* fit, const cpg_opts* opts);
+
+/* One member of a batched CP_ALS call.  Y, A[n], lambda and fit are device
+ * buffers as in cp_als_iter; I and A are host arrays of N entries that are
+ * read during the call only. */
+typedef struct {
+  const void* Y;     /* vec(Y) (eq. 2.1), FP32 (FP64 when precision is CPG_FP64) */
+  int N;             /* order, 2 <= N <= CPG_MAX_ORDER                            */
+  const int64_t* I;  /* host, [N] mode sizes                                      */
+  void* const* A;    /* host, [N] device factors, I_n x R column-major, in place  */
+  double* lambda;    /* device, [R]                                               */
+  int R;             /* rank, 1 <= R <= 64                                        */
+  double* fit;       /* device, [iters] fit after each sweep, or NULL             */
+} cpg_tensor_desc;
+
+/* Workspace bytes for cp_als_batched over these members (opts->precision and
+ * opts->split are read; split applies to every member, 0 = each member's own
+ * n*).  Host-only.  Returns 0 on invalid arguments. */
+size_t cpg_workspace_size_batched(int B, const cpg_tensor_desc* descs, const cpg_opts* opts);
+
+/* `iters` fast CP_ALS sweeps (as cp_als_iter) on each of B independent
+ * tensors of any order, shape and rank.  The paper decomposes one tensor at a
+ * time; batching many small problems is this library's extension of it.
+ *  - Members run concurrently on a pool of streams owned by the library
+ *    (largest members first, each to the least-loaded stream), forked from
+ *    and joined back into opts->stream by events: the whole batch is ordered
+ *    after earlier work on opts->stream and before later work on it, so
+ *    capturing one call on opts->stream into a CUDA graph captures the batch.
+ *  - Each member uses its own slice of opts->workspace; device errors of all
+ *    members go to the one status word at the start of the workspace
+ *    (cpg_device_status).
+ *  - Argument errors of any member (as for cp_als_iter) return before
+ *    anything is launched.
+ * Results are bit-identical to B separate cp_als_iter calls. */
+cpg_status cp_als_batched(int B, const cpg_tensor_desc* descs, int iters, const cpg_opts* opts);
 
 /* Clears the device status word at the start of opts->workspace (stream
  * ordered).  Call once on a new workspace before its first use; the status

@@ -4,6 +4,7 @@ The computation lives in ``libcpgrad.so`` (CUDA, sm_103a) behind the C ABI
 of ``include/cpgrad.h``; ``cpgrad`` is its argument-marshalling binding.
 """
 from .cpgrad import (  # noqa: F401
-    cpg_split_point, cpg_workspace_size, cp_gradient_all, cp_gradient_mode, cp_als_iter, cpg_device_status,
+    cpg_split_point, cpg_workspace_size, cp_gradient_all, cp_gradient_mode, cp_als_iter, cp_als_batched,
+    cpg_device_status,
     colmajor, launch_count, profile_lead, profile_read, Workspace, CpgError, PRECISIONS, lib,
 )

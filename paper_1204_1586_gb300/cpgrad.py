@@ -24,8 +24,8 @@ CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR
 PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4}
 CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS = 0, 1, 2
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
-           "cpg_workspace_init", "cpg_device_status", "cpg_status_str", "cpg_launch_count", "cpg_profile_lead",
-           "cpg_profile_read"]
+           "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
+           "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read"]
 
 
 class CpgError(RuntimeError):
@@ -37,6 +37,12 @@ class CpgError(RuntimeError):
 class cpg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("split", ctypes.c_int), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+class cpg_tensor_desc(ctypes.Structure):
+    _fields_ = [("Y", ctypes.c_void_p), ("N", ctypes.c_int), ("I", ctypes.POINTER(ctypes.c_int64)),
+                ("A", ctypes.POINTER(ctypes.c_void_p)), ("lam", ctypes.c_void_p), ("R", ctypes.c_int),
+                ("fit", ctypes.c_void_p)]
 
 
 _lib = None
@@ -64,6 +70,12 @@ def lib() -> ctypes.CDLL:
         L.cp_als_iter.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cpg_opts)]
         L.cp_als_iter.restype = ctypes.c_int
+        L.cpg_workspace_size_batched.argtypes = [ctypes.c_int, ctypes.POINTER(cpg_tensor_desc),
+                                                 ctypes.POINTER(cpg_opts)]
+        L.cpg_workspace_size_batched.restype = ctypes.c_size_t
+        L.cp_als_batched.argtypes = [ctypes.c_int, ctypes.POINTER(cpg_tensor_desc), ctypes.c_int,
+                                     ctypes.POINTER(cpg_opts)]
+        L.cp_als_batched.restype = ctypes.c_int
         L.cpg_workspace_init.argtypes = [ctypes.POINTER(cpg_opts)]
         L.cpg_workspace_init.restype = ctypes.c_int
         L.cpg_device_status.argtypes = [ctypes.POINTER(cpg_opts)]
@@ -268,6 +280,43 @@ def cp_als_iter(Y, I: Sequence[int], A, iters: int, lam=None, fit=None, *, preci
     if st != CPG_OK:
         raise CpgError(st, "cp_als_iter")
     return lam, fit
+
+
+def cp_als_batched(members, iters: int, *, precision="fp32", split: int = 0, workspace=None, stream=None):
+    """``iters`` fast CP_ALS sweeps on each member, all in one call.  ``members``
+    is a list of (Y, I, A) or (Y, I, A, lam, fit); each A (list of column-major
+    factors) is updated in place.  Returns [(lambda, fit)] per member."""
+    torch = _torch()
+    if len(members) == 0:
+        return []
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    descs = (cpg_tensor_desc * len(members))()
+    keep, out = [], []
+    for b, m in enumerate(members):
+        Y, I, A = m[0], list(m[1]), list(m[2])
+        R = int(A[0].shape[1])
+        _check_y(Y, I, dtype)
+        for n, a in enumerate(A):
+            _check_colmajor(a, int(I[n]), R, dtype, f"member {b}: A[{n}]")
+        lam = m[3] if len(m) > 3 and m[3] is not None else torch.ones(R, dtype=torch.float64, device=Y.device)
+        fit = m[4] if len(m) > 4 and m[4] is not None else torch.zeros(max(int(iters), 1), dtype=torch.float64,
+                                                                        device=Y.device)
+        Ii, Ap = _i64(I), _ptrs(A)
+        keep += [Ii, Ap]
+        descs[b] = cpg_tensor_desc(ctypes.c_void_p(Y.data_ptr()), len(I), Ii, Ap, ctypes.c_void_p(lam.data_ptr()), R,
+                                   ctypes.c_void_p(fit.data_ptr()))
+        out.append((lam, fit))
+    sp = _stream_ptr(stream)
+    ws = _ws_for(workspace, members[0][0].device)
+    o0 = cpg_opts(_prec(precision), int(split), None, 0, None)
+    need = int(lib().cpg_workspace_size_batched(len(members), descs, ctypes.byref(o0)))
+    if need == 0:
+        raise CpgError(CPG_ERR_ARG, "cpg_workspace_size_batched")
+    o = _opts(precision, split, ws, need, sp)
+    st = lib().cp_als_batched(len(members), descs, int(iters), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_als_batched")
+    return out
 
 
 def cpg_device_status(workspace=None, device=None, stream=None) -> int:

@@ -445,13 +445,17 @@ struct SideStream {
   cudaEvent_t done[kMaxOrder] = {};          // side -> main, one per mode
 };
 
-SideStream* side_stream() {
-  static SideStream table[64];
+// Streams of a device's pool for batched calls (slot 0 of the side streams
+// serves single calls, slot 1 + i the pool's stream i).
+constexpr int kPoolStreams = 16;
+
+SideStream* side_stream(int slot = 0) {
+  static SideStream table[64][kPoolStreams + 1];
   static std::mutex mu;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || slot < 0 || slot > kPoolStreams) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  SideStream& ss = table[dev];
+  SideStream& ss = table[dev][slot];
   if (ss.stream == nullptr) {
     if (cudaStreamCreateWithFlags(&ss.stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
@@ -753,7 +757,7 @@ constexpr int kAlsMaxRank = 64;
 
 template <typename T>
 cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, int R, int iters, double* fit,
-                    const cpg_opts* o) {
+                    const cpg_opts* o, int* status_override = nullptr, int side_slot = 0) {
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
   if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
   const int k = choose_split(s, o);
@@ -763,6 +767,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
   if (!lead_fits(lr) || !lead_fits(ll)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  if (status_override) w.h.status = status_override;
   g_status_ptr = w.h.status;
   const void* const* Ac = const_cast<const void* const*>(A);
 
@@ -785,7 +790,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
                          int(als_df_smem_bytes(imax, R)));
     cudaFuncSetAttribute(als_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(als_inv_smem_bytes(R)));
-    side = side_stream();
+    side = side_stream(side_slot);
     if (side == nullptr) return CPG_ERR_CUDA;
   } else {
     cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
@@ -928,6 +933,35 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   return cuda_status(cudaGetLastError());
 }
 
+// ---- batched CP_ALS ------------------------------------------------------------------
+struct StreamPool {
+  cudaStream_t s[kPoolStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kPoolStreams] = {};
+};
+
+StreamPool* stream_pool() {
+  static StreamPool table[64];
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  StreamPool& p = table[dev];
+  if (p.fork == nullptr) {
+    for (int i = 0; i < kPoolStreams; ++i) {
+      if (cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  }
+  return &p;
+}
+
+// Per-member options with the member's workspace slice; 0 bytes on invalid members.
+size_t member_ws_bytes(const cpg_tensor_desc& d, const cpg_opts* opts) {
+  return cpg_workspace_size(d.I, d.N, d.R, opts, CPG_CALL_ALS);
+}
+
 bool ptrs_ok(const void* const* P, int N) {
   if (P == nullptr) return false;
   for (int n = 0; n < N; ++n)
@@ -1065,6 +1099,89 @@ int cpg_profile_read(float* ms, int* sides, int max) {
   }
   g_timing.n = 0;
   return n;
+}
+
+size_t cpg_workspace_size_batched(int B, const cpg_tensor_desc* descs, const cpg_opts* opts) {
+  if (B < 1 || descs == nullptr) return 0;
+  size_t total = kAlign;  // the shared status word
+  for (int b = 0; b < B; ++b) {
+    const size_t m = member_ws_bytes(descs[b], opts);
+    if (m == 0) return 0;
+    total += align_up(m);
+  }
+  return total;
+}
+
+cpg_status cp_als_batched(int B, const cpg_tensor_desc* descs, int iters, const cpg_opts* opts) {
+  if (opts == nullptr || B < 1 || descs == nullptr || iters < 0) return CPG_ERR_ARG;
+  if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
+  if (opts->precision == CPG_TF32X3) return CPG_ERR_UNSUPPORTED;
+  // Validate every member before launching anything.
+  std::vector<Shape> shapes(B);
+  std::vector<size_t> off(B);
+  size_t total = kAlign;
+  for (int b = 0; b < B; ++b) {
+    const cpg_tensor_desc& d = descs[b];
+    cpg_status st = check_shape(d.I, d.N, d.R, shapes[b]);
+    if (st != CPG_OK) return st;
+    if (opts->split != 0 && (opts->split < 1 || opts->split > d.N - 1)) return CPG_ERR_ARG;
+    if (d.Y == nullptr || !ptrs_ok(const_cast<const void* const*>(d.A), d.N) || d.lambda == nullptr)
+      return CPG_ERR_ARG;
+    if (d.R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
+    const size_t m = member_ws_bytes(d, opts);
+    if (m == 0) return CPG_ERR_ARG;
+    off[b] = total;
+    total += align_up(m);
+  }
+  if (opts->workspace == nullptr || opts->workspace_bytes < total) return CPG_ERR_WORKSPACE;
+  if (iters == 0) return CPG_OK;
+  StreamPool* pool = stream_pool();
+  if (pool == nullptr) return CPG_ERR_CUDA;
+  cudaStream_t caller = static_cast<cudaStream_t>(opts->stream);
+  int* status = static_cast<int*>(opts->workspace);
+
+  // Largest members first, each to the stream with the least work so far
+  // (work ~ tensor entries x max(R, 8) per sweep plus a fixed chain cost).
+  std::vector<int> ord(B);
+  for (int b = 0; b < B; ++b) ord[b] = b;
+  auto work = [&](int b) { return double(shapes[b].total) * std::max(descs[b].R, 8) + 2e6 * shapes[b].N; };
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work(x) > work(y); });
+  const int ns = std::min(B, kPoolStreams);
+  std::vector<double> load(ns, 0.0);
+  std::vector<int> used(ns, 0);
+  if (cudaEventRecord(pool->fork, caller) != cudaSuccess) return CPG_ERR_CUDA;
+  cpg_status result = CPG_OK;
+  for (int b : ord) {
+    const int i = int(std::min_element(load.begin(), load.end()) - load.begin());
+    load[i] += work(b);
+    if (!used[i]) {
+      if (cudaStreamWaitEvent(pool->s[i], pool->fork, 0) != cudaSuccess) return CPG_ERR_CUDA;
+      used[i] = 1;
+    }
+    const cpg_tensor_desc& d = descs[b];
+    cpg_opts mo = *opts;
+    mo.workspace = static_cast<char*>(opts->workspace) + off[b];
+    mo.workspace_bytes = total - off[b];
+    mo.stream = pool->s[i];
+    const cpg_status st =
+        is_f64(opts->precision)
+            ? als_impl<double>(shapes[b], static_cast<const double*>(d.Y), d.A, d.lambda, d.R, iters, d.fit, &mo,
+                               status, 1 + i)
+            : als_impl<float>(shapes[b], static_cast<const float*>(d.Y), d.A, d.lambda, d.R, iters, d.fit, &mo, status,
+                              1 + i);
+    if (st != CPG_OK) {
+      result = st;
+      break;
+    }
+  }
+  // Join every stream that was forked, whatever happened above.
+  for (int i = 0; i < ns; ++i) {
+    if (!used[i]) continue;
+    if (cudaEventRecord(pool->join[i], pool->s[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(caller, pool->join[i], 0) != cudaSuccess)
+      result = CPG_ERR_CUDA;
+  }
+  return result;
 }
 
 uint64_t cpg_launch_count(int reset) {

@@ -111,6 +111,43 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.cpg_device_status(None) == cpgrad.CPG_ERR_ARG
 
 
+def _desc(I, R, Y=16, A=None, lam=32):
+    Ii = cpgrad._i64(I)
+    Ap = A if A is not None else (ctypes.c_void_p * len(I))(*([ctypes.c_void_p(16)] * len(I)))
+    d = cpgrad.cpg_tensor_desc(ctypes.c_void_p(Y) if Y else None, len(I), Ii, Ap,
+                               ctypes.c_void_p(lam) if lam else None, R, None)
+    return d, (Ii, Ap)
+
+
+def test_batched_workspace_and_argument_errors(L):
+    keep = []
+    members = [([4, 5, 6], 3), ([7, 3, 2, 5], 8), ([30, 40], 2)]
+    descs = (cpgrad.cpg_tensor_desc * len(members))()
+    for b, (I, R) in enumerate(members):
+        descs[b], k = _desc(I, R)
+        keep.append(k)
+    o = _opts()
+    total = L.cpg_workspace_size_batched(len(members), descs, ctypes.byref(o))
+    each = [cpgrad.cpg_workspace_size(I, R, "fp32", 0, cpgrad.CALL_ALS) for I, R in members]
+    # the shared status word plus every member's ALS workspace (256-byte aligned)
+    assert total >= 256 + sum(each) and total <= 256 + sum(each) + 256 * len(members)
+    assert L.cpg_workspace_size_batched(0, descs, ctypes.byref(o)) == 0
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cp_als_batched(len(members), descs, 2, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_als_batched(0, descs, 2, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_als_batched(len(members), descs, -1, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_als_batched(len(members), descs, 2, None) == cpgrad.CPG_ERR_ARG
+    bad = (cpgrad.cpg_tensor_desc * 2)()
+    bad[0], k0 = _desc([4, 5, 6], 3)
+    bad[1], k1 = _desc([4, 5, 6], 3, lam=0)     # null lambda in the second member
+    assert L.cp_als_batched(2, bad, 2, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    bad[1], k1 = _desc([4, 5, 6], 65)           # rank above the ALS limit
+    assert L.cp_als_batched(2, bad, 2, ctypes.byref(o)) == cpgrad.CPG_ERR_UNSUPPORTED
+    bad[1], k1 = _desc([4], 3)                  # order 1
+    assert L.cp_als_batched(2, bad, 2, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert cpgrad.launch_count() == 0 * n0
+
+
 def test_status_strings(L):
     for s in range(8):
         assert cpgrad.status_str(s)

@@ -1,0 +1,91 @@
+"""GPU checks of cp_als_batched: many independent tensors of mixed order,
+shape and rank in one call give exactly the results of one cp_als_iter call
+per tensor (same kernels, fixed summation orders), and match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import cpsynth
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1204_1586_gb300 as m
+    return m
+
+
+def dev_factor(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a.T).astype(dtype)).cuda().t()
+
+
+def mixed_batch(count, seed, dtype, orders=(2, 3, 4, 5)):
+    """Members with N in {2..5}, I_n in [3, 24], R in [1, min(12, min I_n)]
+    (so that every normal-equation matrix is positive definite), each a
+    rank-R CP model plus 20 dB noise, and a seeded N(0,1) start."""
+    rng = cpsynth.rng(seed, 99)
+    out = []
+    for b in range(count):
+        N = int(rng.choice(orders))
+        I = [int(v) for v in rng.integers(3, 25, size=N)]
+        R = int(rng.integers(1, min(12, min(I)) + 1))
+        out.append(cpsynth.make_problem(I, R, snr_db=20.0, seed=seed * 1000 + b, dtype=dtype))
+    return out
+
+
+@pytest.mark.parametrize("prec,count", [("fp32", 7), ("fp32", 40), ("fp64", 5), ("bf16x3", 6)])
+def test_batched_equals_separate_calls(cg, prec, count):
+    dt = np.float64 if prec == "fp64" else np.float32
+    probs = mixed_batch(count, seed=3 + count, dtype=dt)
+    iters = 4
+    Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+    A_b = [[dev_factor(a, dt) for a in p.init] for p in probs]
+    A_s = [[a.clone() for a in A] for A in A_b]
+    res_b = cg.cp_als_batched([(Y, p.I, A) for Y, p, A in zip(Ys, probs, A_b)], iters, precision=prec)
+    res_s = [cg.cp_als_iter(Y, p.I, A, iters, precision=prec) for Y, p, A in zip(Ys, probs, A_s)]
+    torch.cuda.synchronize()
+    assert cg.cpg_device_status() == 0
+    for b in range(count):
+        for a1, a2 in zip(A_b[b], A_s[b]):
+            assert torch.equal(a1, a2), b
+        assert torch.equal(res_b[b][0], res_s[b][0]), b
+        assert torch.equal(res_b[b][1], res_s[b][1]), b
+
+
+def test_batched_matches_oracle(cg):
+    # Orders >= 3: an order-2 member with R = min(I) is fitted exactly, where
+    # the cheap fit formula's cancellation (about sqrt(FP32 epsilon)) would
+    # dominate the comparison.
+    probs = mixed_batch(5, seed=11, dtype=np.float32, orders=(3, 4, 5))
+    iters = 3
+    Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+    A_b = [[dev_factor(a, np.float32) for a in p.init] for p in probs]
+    res = cg.cp_als_batched([(Y, p.I, A) for Y, p, A in zip(Ys, probs, A_b)], iters)
+    torch.cuda.synchronize()
+    for b, p in enumerate(probs):
+        tr = oracle.cp_als(p.y.astype(np.float64), p.I, p.init, iters=iters)
+        fit = res[b][1].cpu().numpy()[:iters]
+        assert np.max(np.abs(fit - np.array(tr.fits))) <= 1e-5, (b, fit, tr.fits)
+        for n in range(len(p.I)):
+            got = A_b[b][n].double().cpu().numpy()
+            assert np.linalg.norm(got - tr.A[n]) <= 1e-4 * max(1.0, np.linalg.norm(tr.A[n])), (b, n)
+
+
+def test_batched_is_ordered_on_the_caller_stream(cg):
+    """Work enqueued on the caller's stream after the call sees the results."""
+    probs = mixed_batch(20, seed=5, dtype=np.float32)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+        A_b = [[dev_factor(a, np.float32) for a in p.init] for p in probs]
+        res = cg.cp_als_batched([(Y, p.I, A) for Y, p, A in zip(Ys, probs, A_b)], 2, stream=s)
+        snap = [A[0].clone() for A in A_b]  # ordered after the batch on s
+    s.synchronize()
+    for b in range(len(probs)):
+        assert torch.equal(snap[b], A_b[b][0])
