@@ -465,14 +465,16 @@ def run_batched(args):
     ws = cg.Workspace(dev)
     stream = torch.cuda.current_stream()
 
+    prec = args.precision
+
     def step_batched():
         flat.copy_(flat0)
-        cg.cp_als_batched(members, BATCH_ITERS, workspace=ws)
+        cg.cp_als_batched(members, BATCH_ITERS, workspace=ws, precision=prec)
 
     def step_serial():
         flat.copy_(flat0)
         for Y, I, a, lam, fit in members:
-            cg.cp_als_iter(Y, I, a, BATCH_ITERS, lam, fit, workspace=ws)
+            cg.cp_als_iter(Y, I, a, BATCH_ITERS, lam, fit, workspace=ws, precision=prec)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -497,7 +499,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            cg.cp_als_batched(members, BATCH_ITERS, workspace=ws)
+            cg.cp_als_batched(members, BATCH_ITERS, workspace=ws, precision=prec)
         ms_graph = timed(lambda: (flat.copy_(flat0), g.replay()), args.steps, 2)
     except Exception as ex:  # report, keep the other numbers
         graph_note = f"capture failed: {str(ex)[:160]}"
@@ -511,7 +513,8 @@ def run_batched(args):
         "config": {"workload": f"batched: {len(probs)} FP32 tensors, order 3-5, I_n in [8, 64], R in [4, 32], "
                                f"rank-R N(0,1) CP models + 20 dB noise; {BATCH_ITERS} fast CP_ALS sweeps each per step",
                    "members": len(probs), "entries": entries, "bytes": 4 * entries, "als_iters": BATCH_ITERS,
-                   "l2": "inputs larger than L2 (%.1f GB)" % (4 * entries / 1e9), "generation_s": round(gen_s, 1)},
+                   "l2": "inputs larger than L2 (%.1f GB)" % (4 * entries / 1e9), "generation_s": round(gen_s, 1),
+                   "precision": prec},
         "effective_GBps": gbytes / (ms_batched / 1e3),
         "per_member_calls_ms": ms_serial, "graph_replay_ms": ms_graph, "graph_note": graph_note,
         "speedup_vs_per_member_calls": ms_serial / ms_batched,
