@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
                     help="arithmetic of the leading contraction (Algorithm 2 steps 4/7)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run for ncu: warm-up and timed steps only, no e2e, checks or CPU baseline")
@@ -362,8 +362,8 @@ def main():
         per_side.setdefault({1: "step4_R", 2: "step7_L", 3: "step4+7_fused"}[s], []).append(t)
     avg = sum(lead_ms) / len(lead_ms) if lead_ms else float("nan")
     achieved = ybytes / (avg / 1e3) / 1e9
-    # The split-BF16 forms run the tensor-core kernel (J = 10^4 rows are whole 16-byte chunks).
-    kernel = "lead_simt_kernel" if prec == "fp32" else "lead_tc_kernel"
+    # The split forms run the tensor-core kernels (J = 10^4 rows are whole 16-byte chunks).
+    kernel = {"fp32": "lead_simt_kernel", "tf32x3": "lead_tf32_kernel"}.get(prec, "lead_tc_kernel")
     traffic = lead_traffic(kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": f"{kernel} (Algorithm 2 steps 4/7)",
@@ -422,6 +422,7 @@ LEAD_KERNELS = {
     # kernel family -> (sources whose hash identifies the captured build, traffic summary)
     "lead_simt_kernel": (("lead_simt.cuh", "common.cuh", "tc_common.cuh"), "lead_simt_traffic.json"),
     "lead_tc_kernel": (("lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tc_traffic.json"),
+    "lead_tf32_kernel": (("lead_tf32.cuh", "lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tf32_traffic.json"),
 }
 
 

@@ -89,8 +89,8 @@ bool is_f64(int prec) { return prec == CPG_FP64; }
 
 // ---- leading-pass plan ----------------------------------------------------------
 struct LeadPlan {
-  bool tc = false;  // tensor-core kernel (split BF16 products)
-  int tc_prec = 0;  // 0 = BF16x3, 1 = BF16
+  bool tc = false;  // tensor-core kernel (split BF16 / TF32 products)
+  int tc_prec = 0;  // 0 = BF16x3, 1 = BF16, 2 = TF32x3
   int RTP = 0;      // tensor-core rank tile
   int k = 0, sides = 0;
   int64_t J = 0, K = 0;
@@ -105,7 +105,7 @@ SimtShape shape_for(int prec, int r, int sides) {
   return is_f64(prec) ? simt_shape_f64(r, sides) : simt_shape_f32(r, sides);
 }
 
-bool is_tc_prec(int prec) { return prec == CPG_BF16X3 || prec == CPG_BF16; }
+bool is_tc_prec(int prec) { return prec == CPG_BF16X3 || prec == CPG_BF16 || prec == CPG_TF32X3; }
 
 // Grid over (J-blocks, K-splits): the K-split count that best fills `slots`
 // resident CTAs, discounting CTAs that run only a few stages.
@@ -182,7 +182,7 @@ void choose_grid(LeadPlan& p, int R, int esize, int slots) {
 LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   LeadPlan p;
   p.tc = true;
-  p.tc_prec = (prec == CPG_BF16X3) ? 0 : 1;
+  p.tc_prec = (prec == CPG_BF16X3) ? 0 : (prec == CPG_BF16) ? 1 : 2;
   p.k = k;
   p.sides = sides;
   p.J = prod(s, 0, k);
@@ -190,17 +190,17 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   p.RTmax = 64;
   p.groups = (R + p.RTmax - 1) / p.RTmax;
   p.RTP = tc_rank_tile(std::min(R, p.RTmax));
-  p.TJ = 128;
-  p.TK = 128;
-  const int64_t tiles = (p.J + 127) / 128;
+  p.TJ = tc_tile_rows(p.tc_prec, sides);
+  p.TK = tc_tile_cols(p.tc_prec, sides);
+  const int64_t tiles = (p.J + p.TJ - 1) / p.TJ;
   if (sides == 2) {
     // Step 7 alone: row tiles outer, one tensor-memory accumulator per column
     // chunk (at most 512 / NW chunks per CTA), W_L built once per row tile.
     // Minimise waves * (super-stages + W_L builds + fixed cost) + partial-sum
     // traffic, as choose_grid does for the CUDA-core kernel (1 CTA per SM).
-    const int nw = p.tc_prec == 0 ? 2 * p.RTP : p.RTP;
+    const int nw = p.tc_prec == 1 ? p.RTP : 2 * p.RTP;
     const int64_t max_per = std::max(1, 512 / nw);
-    const int64_t chunks = (p.K + 127) / 128;
+    const int64_t chunks = (p.K + p.TK - 1) / p.TK;
     const int slots = num_sms();
     const double wbuild = 0.25 * p.RTP / 16.0;  // one W_L build, in super-stages
     double best = 1e300;
@@ -217,7 +217,8 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
         if (nJb > 65535 || nCb > 65535) continue;
         const double waves = double((nJb * nCb + slots - 1) / slots);
         const double partial = 2.0 * double(nJb) * R * double(p.K) * 4.0;
-        const double cost = waves * (double(per * nrt) + double(nrt) * wbuild + 2.0) + partial / (double(slots) * 65536.0);
+        const double stage_bytes = double(p.TJ) * p.TK * 4.0;
+        const double cost = waves * (double(per * nrt) + double(nrt) * wbuild + 2.0) + partial / (double(slots) * stage_bytes);
         if (cost < best - 1e-9) {
           best = cost;
           best_nrt = nrt;
@@ -227,11 +228,11 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
     p.nrt = int(best_nrt);
     p.nJb = int((tiles + best_nrt - 1) / best_nrt);
     p.nKs = int((chunks + best_per - 1) / best_per);
-    p.Kc = best_per * 128;
+    p.Kc = best_per * p.TK;
   } else {
     const int cap = std::min(tc_max_nrt(p.RTP, sides, p.tc_prec), 8);
     p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
-    p.nJb = int((p.J + 128LL * p.nrt - 1) / (128LL * p.nrt));
+    p.nJb = int((p.J + int64_t(p.TJ) * p.nrt - 1) / (int64_t(p.TJ) * p.nrt));
     choose_ksplit(p, num_sms());
   }
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
@@ -361,6 +362,7 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
 // Fused pass unless its J-block partials would cost more than a fifth of Y's
 // bytes; then the two sides run as separate passes (the L pass with tall blocks).
 bool use_fused(const Shape& s, int R, int k, int prec) {
+  if (prec == CPG_TF32X3) return false;  // the split-TF32 kernel runs one side per pass
   const LeadPlan f = plan_lead(s, R, k, 3, prec);
   return double(f.lpart_elems + f.rpart_elems) <= 0.2 * double(s.total);
 }
@@ -644,7 +646,6 @@ cpg_status common_checks(const cpg_opts* opts, Shape& s, const int64_t* I, int N
   if (st != CPG_OK) return st;
   if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
   if (opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return CPG_ERR_ARG;
-  if (opts->precision == CPG_TF32X3) return CPG_ERR_UNSUPPORTED;
   return CPG_OK;
 }
 
@@ -1115,7 +1116,6 @@ size_t cpg_workspace_size_batched(int B, const cpg_tensor_desc* descs, const cpg
 cpg_status cp_als_batched(int B, const cpg_tensor_desc* descs, int iters, const cpg_opts* opts) {
   if (opts == nullptr || B < 1 || descs == nullptr || iters < 0) return CPG_ERR_ARG;
   if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
-  if (opts->precision == CPG_TF32X3) return CPG_ERR_UNSUPPORTED;
   // Validate every member before launching anything.
   std::vector<Shape> shapes(B);
   std::vector<size_t> off(B);

@@ -1,5 +1,6 @@
 // Host side of the tensor-core leading contraction: TMA tensor map of Y and
-// the kernel instances (rank tile 16 / 32 / 64, sides, BF16x3 or BF16).
+// the kernel instances (rank tile 16 / 32 / 64, sides, BF16x3 or BF16); the
+// split-TF32 form is forwarded to lead_tf32.cu.
 #include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
 #include "tensor_map.h"
@@ -43,12 +44,16 @@ cudaError_t run_prec(const CUtensorMap& m, const TcArgs& a, int sides, int prec,
 int tc_rank_tile(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 
 int tc_max_nrt(int RTP, int sides, int prec) {
-  const int nw = (prec == 0) ? 2 * RTP : RTP;
+  const int nw = (prec == 1) ? RTP : 2 * RTP;
   if (sides == 2) return 1 << 20;     // row tiles are outer: any number per CTA
   return sides == 1 ? 512 / nw : 512 / nw - 2;  // fused: two step-7 accumulators
 }
 
+int tc_tile_rows(int prec, int sides) { return prec == 2 ? (sides == 1 ? 128 : 64) : 128; }
+int tc_tile_cols(int prec, int sides) { return prec == 2 ? (sides == 1 ? 64 : 128) : 128; }
+
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {
+  if (prec == 2) return launch_lead_tf32(Y, a, RTP, sides, grid, st);
   CUtensorMap m{};
   TcArgs b = a;
   b.Y = Y;

@@ -86,6 +86,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A[smem] * B[smem], kind::tf32 (TF32 inputs in 32-bit
+// containers with the low 13 mantissa bits zero, FP32 accumulate).
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrives on `bar` once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
@@ -127,6 +138,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, int a_mn, in
   return (1u << 4)                         // D format: F32
          | (1u << 7)                       // A format: BF16
          | (1u << 10)                      // B format: BF16
+         | (uint32_t(a_mn & 1) << 15)      // A major
+         | (uint32_t(b_mn & 1) << 16)      // B major
+         | (uint32_t(N >> 3) << 17)        // N / 8
+         | (uint32_t(M >> 4) << 24);       // M / 16
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, dense.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4)                         // D format: F32
+         | (2u << 7)                       // A format: TF32
+         | (2u << 10)                      // B format: TF32
          | (uint32_t(a_mn & 1) << 15)      // A major
          | (uint32_t(b_mn & 1) << 16)      // B major
          | (uint32_t(N >> 3) << 17)        // N / 8

@@ -101,9 +101,7 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.cp_als_iter(dummy, I, 3, A, lam, 3, 0, None, ctypes.byref(o)) == cpgrad.CPG_OK     # nothing to do
     assert L.cp_als_iter(dummy, I, 3, A, lam, 3, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
     assert L.cp_als_iter(dummy, I, 3, A, lam, 65, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_UNSUPPORTED
-    op = _opts(prec=1)       # 3xTF32 has no kernel
-    assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(op)) == cpgrad.CPG_ERR_UNSUPPORTED
-    for prec in (2, 3):      # split-BF16 forms: argument checks pass, the missing workspace is reported
+    for prec in (1, 2, 3):   # split TF32 / BF16 forms: argument checks pass, the missing workspace is reported
         op = _opts(prec=prec)
         assert L.cp_gradient_all(dummy, I, 3, A, 3, G, ctypes.byref(op)) == cpgrad.CPG_ERR_WORKSPACE
     assert cpgrad.launch_count() == n0 * 0  # nothing was launched

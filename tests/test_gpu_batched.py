@@ -39,7 +39,7 @@ def mixed_batch(count, seed, dtype, orders=(2, 3, 4, 5)):
     return out
 
 
-@pytest.mark.parametrize("prec,count", [("fp32", 7), ("fp32", 40), ("fp64", 5), ("bf16x3", 6)])
+@pytest.mark.parametrize("prec,count", [("fp32", 7), ("fp32", 40), ("fp64", 5), ("bf16x3", 6), ("tf32x3", 6)])
 def test_batched_equals_separate_calls(cg, prec, count):
     dt = np.float64 if prec == "fp64" else np.float32
     probs = mixed_batch(count, seed=3 + count, dtype=dt)

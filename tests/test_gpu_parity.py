@@ -1,7 +1,8 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances: relative Frobenius error per mode <= 1e-5 for the FP32 path and
-<= 1e-12 for the FP64 path (the bounds the method's target states for FP32
+the split BF16x3 / TF32x3 products, 2e-2 for pure BF16, and <= 1e-12 for the
+FP64 path (the bounds the method's target states for FP32
 and a choice for FP64).  ALS fits agree within 1e-5 (FP32) / 1e-9 (FP64)."""
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "fp64": 1e-12, "bf16x3": 1e-5, "bf16": 2e-2}
+TOL = {"fp32": 1e-5, "fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +76,15 @@ GRAD_CASES = [
     ([20, 12, 40, 36], 33, "bf16x3"),   # rank tile 64, R not a multiple of 16
     ([40, 36, 28, 20], 16, "bf16"),
     ([100, 100, 100], 10, "bf16"),
+    # split-TF32 products on the tensor cores (one side per pass; 128 x 64
+    # step-4 tiles, 64 x 128 step-7 tiles)
+    ([24, 20, 30, 17], 12, "tf32x3"),   # k=2, J=480: TMA boxes, ragged row tile and column chunk
+    ([100, 100, 100], 20, "tf32x3"),    # k=1, J=100, rank tile 32
+    ([64, 64, 64, 4], 3, "tf32x3"),     # k=1, J=64, K=16384: many column chunks
+    ([12, 11, 10, 9], 64, "tf32x3"),    # rank tile 64
+    ([9, 10, 11], 70, "tf32x3"),        # J=9: element copies, two rank groups
+    ([15, 15, 15, 15, 15], 10, "tf32x3"),  # J=225: element copies
+    ([20, 12, 40, 36], 33, "tf32x3"),   # rank tile 64, R not a multiple of 16
 ]
 
 
@@ -106,7 +116,8 @@ def test_gradient_all_split_override(cg, split):
 @pytest.mark.parametrize("I,R,prec", [([30, 40, 50], 5, "fp32"), ([11, 9, 13, 7, 5], 9, "fp32"),
                                       ([200, 3, 4], 6, "fp32"), ([3, 4, 200], 6, "fp32"),
                                       ([13, 7, 9, 11], 8, "fp64"), ([40, 12, 8, 20], 8, "bf16x3"),
-                                      ([4, 8, 300], 6, "bf16x3")])
+                                      ([4, 8, 300], 6, "bf16x3"), ([40, 12, 8, 20], 8, "tf32x3"),
+                                      ([4, 8, 300], 6, "tf32x3")])
 def test_gradient_mode(cg, I, R, prec):
     y, A, dt = inputs(I, R, prec, seed=5)
     Y = torch.from_numpy(y).cuda()
@@ -144,7 +155,7 @@ def test_gradient_deterministic(cg):
 
 
 @pytest.mark.parametrize("R", [10, 20])
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16"])
 def test_precision_study_7d(cg, R, prec):
     """The 7-D collinear workload's recipe (factor columns with pairwise
     cosine 0.5, 30 dB noise) at I = 7 per mode: per-mode relative Frobenius
@@ -162,7 +173,7 @@ def test_precision_study_7d(cg, R, prec):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3"])
 def test_gradient_full_size_sampled(cg, prec):
     """The 4-D 100^4, R = 10 workload in the benchmark's launch configuration;
     sampled entries g_r^(n)[i] checked one by one with the oracle (eq. 3.2)."""
@@ -192,7 +203,8 @@ def test_gradient_full_size_sampled(cg, prec):
 
 @pytest.mark.parametrize("I,R,prec,iters", [([30, 40, 50], 5, "fp64", 10), ([24, 20, 30, 17], 6, "fp32", 6),
                                             ([12, 10, 8, 9, 7], 4, "fp32", 5), ([40, 30], 3, "fp32", 8),
-                                            ([24, 20, 30, 17], 6, "bf16x3", 6), ([40, 36, 28], 5, "bf16x3", 5)])
+                                            ([24, 20, 30, 17], 6, "bf16x3", 6), ([40, 36, 28], 5, "bf16x3", 5),
+                                            ([24, 20, 30, 17], 6, "tf32x3", 6), ([40, 36, 28], 5, "tf32x3", 5)])
 def test_als_matches_oracle(cg, I, R, prec, iters):
     dt = np.float64 if prec == "fp64" else np.float32
     p = cpsynth.make_problem(I, R, snr_db=20.0, seed=11, dtype=dt)
@@ -203,7 +215,7 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=iters)
     # Gauss-Seidel sweeps feed each gradient's error into the next factors, so
     # the split product's ~1e-6 gradient error grows along the trajectory.
-    ftol = {"fp64": 1e-9, "fp32": 1e-5, "bf16x3": 1e-4}[prec]
+    ftol = {"fp64": 1e-9, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}[prec]
     np.testing.assert_allclose(fit.cpu().numpy(), tr.fits, atol=ftol)
     if prec == "fp64":
         for n in range(len(I)):
@@ -212,7 +224,7 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     assert cg.cpg_device_status() == 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
 def test_als_one_sweep_factors(cg, prec):
     """Per-sweep parity from identical factors."""
     I, R = [24, 20, 30, 17], 6
@@ -224,7 +236,7 @@ def test_als_one_sweep_factors(cg, prec):
     for n in range(len(I)):
         assert rel(Ad[n].double().cpu().numpy(), tr.A[n]) <= 1e-5, n
     # lambda is the norm of G V^{-1}: the solve amplifies the split product's error
-    np.testing.assert_allclose(lam.cpu().numpy(), tr.lam, rtol={"fp32": 1e-5, "bf16x3": 5e-5}[prec])
+    np.testing.assert_allclose(lam.cpu().numpy(), tr.lam, rtol={"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 5e-5}[prec])
 
 
 def test_als_noiseless_fit_to_one(cg):
