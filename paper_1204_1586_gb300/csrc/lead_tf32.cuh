@@ -246,13 +246,15 @@ __global__ void __launch_bounds__(256, 1) lead_tf32_kernel(const __grid_constant
     if constexpr (DO_R) {
       // Blocks of 4 rows x 4 columns, transposed in registers into the
       // K-major [hi | lo] buffer (row j, column c at tf32_wtile_off(j, c)).
-      // A warp reads 8 consecutive chunks of 4 lines and writes rows with
-      // 8 distinct chunk positions: no bank conflicts beyond 16-byte accesses.
+      // Lane l of an 8-lane group g takes row quad jq = l and column quad
+      // (g + l / 2) mod 16: its reads (chunk jq ^ (column mod 8)) and its
+      // writes (chunk (column quad mod 8) ^ (row mod 8)) then fall on 8
+      // distinct 16-byte bank groups, so 16-byte accesses are conflict-free.
       unsigned char* conv = sm + C::OFF_CONV;
 #pragma unroll
       for (int u = 0; u < (C::TJS / 4) * (C::TKS / 4) / NT; ++u) {
         const int blk = tid + NT * u;
-        const int jq = blk & 7, cq = (blk >> 3) & 15, x = blk >> 7;
+        const int jq = blk & 7, cq = (((blk >> 3) & 15) + (jq >> 1)) & 15, x = blk >> 7;
         const int j = 32 * x + 4 * jq, c = 4 * cq;
         float4 v[4];
 #pragma unroll
