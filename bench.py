@@ -356,6 +356,7 @@ def main():
 
     hbm, peak_kind = peaks()
     ybytes = 4 * prod(I)
+    lead = [(t, s) for t, s in lead if s in (1, 2, 3)]
     lead_ms = [t for t, _ in lead]
     per_side = {}
     for t, s in lead:
@@ -401,6 +402,22 @@ def main():
         "clocks": clocks,
         "check": check,
     }
+    # Every launch of one more step, event-timed one by one on its stream
+    # (outside the timed region): where a step's time goes, per kind of kernel.
+    cg.profile_lead(2)
+    step(Y)
+    torch.cuda.synchronize()
+    rec = cg.profile_read()
+    cg.profile_lead(False)
+    brk = {}
+    for t, kind in rec:
+        name = cg.LAUNCH_KINDS.get(kind, str(kind))
+        e = brk.setdefault(name, {"launches": 0, "us": 0.0})
+        e["launches"] += 1
+        e["us"] += 1e3 * t
+    line["step_breakdown"] = {"note": "one step, each launch bracketed by CUDA events (kernel time; the rest "
+                                      "of the step is launch gaps)", "kinds": brk,
+                              "kernel_us_total": sum(e["us"] for e in brk.values())}
     # per-component timing outside the timed region (informational)
     tg = _time_component(lambda: cg.cp_gradient_all(Y, I, A0, G, workspace=ws, precision=prec), stream)
     ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 10, workspace=ws, precision=prec),

@@ -174,19 +174,30 @@ const char* cpg_status_str(int status);
  * last reset (counts what the host enqueued; for benchmarks). */
 uint64_t cpg_launch_count(int reset);
 
-/* Benchmark instrumentation of the leading contraction (Algorithm 2 steps 4
- * and 7, the kernel that streams Y).  While enabled, every leading-pass launch
- * is bracketed by two CUDA events recorded on its own stream (at most 4096
- * launches are kept).  enable = 1 creates the events on first use and starts
- * a new record; 0 stops recording.  Returns CPG_OK or CPG_ERR_CUDA.
+/* Benchmark instrumentation.  While enabled, launches are bracketed by two
+ * CUDA events recorded on their own stream (at most 4096 launches are kept):
+ * enable = 1 records the leading contraction (Algorithm 2 steps 4 and 7, the
+ * kernel that streams Y), enable = 2 records every kernel of the library.
+ * A nonzero enable creates the events on first use and starts a new record;
+ * 0 stops recording.  Returns CPG_OK or CPG_ERR_CUDA.
  * Not thread-safe: one recording thread at a time. */
 int cpg_profile_lead(int enable);
 
+/* Kinds of recorded launches (cpg_profile_read). */
+#define CPG_KIND_LEAD_R 1       /* leading pass, step 4 only                    */
+#define CPG_KIND_LEAD_L 2       /* leading pass, step 7 only                    */
+#define CPG_KIND_LEAD_FUSED 3   /* leading pass, steps 4 and 7 from one read    */
+#define CPG_KIND_CHAIN 10       /* finishing contraction or recursion           */
+#define CPG_KIND_MODE 11        /* CP_ALS mode, FP32 data: G and the update     */
+#define CPG_KIND_GRAM 12        /* Gram matrices                                */
+#define CPG_KIND_KRON 13        /* Kronecker vector of a run of modes           */
+#define CPG_KIND_NORM 14        /* ||Y||^2                                      */
+#define CPG_KIND_UPDATE 15      /* CP_ALS update, FP64 data                     */
+
 /* Waits for and returns the recorded launch durations in milliseconds
- * (ms[i]) and the sides each launch computed (sides[i]: 1 = step 4 only,
- * 2 = step 7 only, 3 = both), at most `max` entries, then clears the record.
- * Either array may be NULL.  Returns the number of entries, or -1 on a CUDA
- * error. */
+ * (ms[i]) and each launch's kind (sides[i], CPG_KIND_*), at most `max`
+ * entries in launch order, then clears the record.  Either array may be
+ * NULL.  Returns the number of entries, or -1 on a CUDA error. */
 int cpg_profile_read(float* ms, int* sides, int max);
 
 /* Size of the fixed device scratch array used by cp_gradient_all_noalloc

@@ -121,15 +121,22 @@ def launch_count(reset: bool = False) -> int:
     return int(lib().cpg_launch_count(1 if reset else 0))
 
 
-def profile_lead(enable: bool) -> None:
-    """Start (True) or stop (False) event timing of leading-pass launches."""
-    st = lib().cpg_profile_lead(1 if enable else 0)
+# Launch kinds of the timing record (cpgrad.h CPG_KIND_*).
+LAUNCH_KINDS = {1: "lead_step4_R", 2: "lead_step7_L", 3: "lead_step4+7_fused", 10: "chain_segmented_dot",
+                11: "als_mode_fused_update", 12: "gram", 13: "kronecker_vector", 14: "norm_y2", 15: "als_update_fp64"}
+
+
+def profile_lead(enable) -> None:
+    """Event timing of launches: True / 1 = leading passes only, 2 = every
+    kernel of the library, False / 0 = stop."""
+    mode = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+    st = lib().cpg_profile_lead(mode)
     if st != CPG_OK:
         raise CpgError(st, "cpg_profile_lead")
 
 
 def profile_read(max_entries: int = 4096):
-    """[(milliseconds, sides)] of the leading-pass launches recorded since profile_lead(True)."""
+    """[(milliseconds, kind)] of the launches recorded since profile_lead(...), in launch order."""
     ms = (ctypes.c_float * max_entries)()
     sd = (ctypes.c_int * max_entries)()
     n = lib().cpg_profile_read(ms, sd, max_entries)

@@ -1,11 +1,10 @@
 // CP_ALS factor update (eq. 2.14, fast ALS of Section 4) for FP32 tensors,
 // with the normal equations carried in double-float arithmetic (dfloat.cuh).
 //
-// For mode n, with the gradient G = Y_(n) KR from the chain kernels:
+// For mode n, with the gradient G = Y_(n) KR from the chain:
 //   V        = Hadamard_{m != n} Gram_m          (Gram_m = A^(m)T A^(m))
-//   V^{-1}   by Gauss-Jordan elimination of [V | I] (als_inverse_df_kernel,
-//            which needs only the Grams and so can run ahead of G)
-//   X        = G V^{-1}                          (als_update_df_kernel, below)
+//   V^{-1}   by Gauss-Jordan elimination of [V | I]
+//   X        = G V^{-1}
 //   lambda_q = ||x_q||,  a_q = x_q / lambda_q    (column normalisation)
 //   Gram_n   = A^(n)T A^(n) of the stored FP32 factor (products exact, sums compensated)
 // and after the last mode of a sweep the fit from R x R quantities:
@@ -23,6 +22,13 @@
 // the FP32 pipe; the measured FP64 rate of this GPU (64-cycle dependent FMA,
 // ~680-cycle divide) would put tens of microseconds on the critical path of
 // every update.
+//
+// The update runs inside the kernel that produces G (als_mode_df_kernel):
+// every CTA but one computes its share of G (a finishing contraction or a
+// recursion of the chain, chain.cuh) while the extra CTA forms V and V^{-1}
+// (they need only the Grams, final before the launch); the CTA that finishes
+// last, found by an atomic ticket after a memory fence (no CTA ever waits for
+// another), then updates the factor.  One launch per mode, no second stream.
 #pragma once
 
 #include "chain.cuh"
@@ -35,9 +41,9 @@ struct AlsDfArgs {
   int N, n, R;
   int64_t In;
   df* grams;              // [N][R][R] double-float Grams
-  const df* Vi;           // [R][R] V^{-1} of this mode (from als_inverse_df_kernel)
-  const df* V;            // [R][R] V of this mode
-  const float* G;         // In x R, column-major
+  df* V;                  // [R][R] V of this mode (written by the inverse CTA)
+  df* Vi;                 // [R][R] V^{-1}; Vi[0] = 0 marks a V that is not positive definite
+  const float* G;         // In x R, column-major (read through L2: other CTAs wrote it)
   float* An;              // In x R, column-major (updated in place)
   double* lambda;         // [R]
   int* status;            // device status word
@@ -58,27 +64,20 @@ __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
   grams[(int64_t(m) * R + b) * R + a] = s;
 }
 
-// ---- V and V^{-1} of one mode ------------------------------------------------------
-constexpr int kInvThreads = 256;
-
-inline size_t als_inv_smem_bytes(int R) { return (2 * size_t(R) * R + 2 * size_t(R) + 4 * size_t(R)) * sizeof(df); }
-
-// V = Hadamard_{m != n} Gram_m and V^{-1} by Gauss-Jordan elimination of
-// [V | I]; one block of kInvThreads threads, als_inv_smem_bytes(R) of shared
-// memory.  Writes V and V^{-1} ([R][R], symmetric); a pivot that is not
-// positive (V not positive definite) records CPG_ERR_SINGULAR and writes a
-// zero pivot marker (Vi[0] = 0) that the update kernel checks.
-// Step j of the elimination touches only the R columns j+1 .. R+j (earlier left
-// columns are finished unit vectors, later right columns are still identity
-// columns) and reads row j and column j from side buffers written by step
-// j - 1, so every entry updates in place with one barrier per step.
-__global__ void __launch_bounds__(kInvThreads) als_inverse_df_kernel(const df* grams, int N, int n, int R, df* V,
-                                                                      df* Vi, int* status) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+// ---- V and V^{-1} of one mode, by one block ----------------------------------------
+// V = Hadamard_{m != n} Gram_m into Vs and V^{-1} into Vis ([R][R], symmetric,
+// Vis[p + R q]), by Gauss-Jordan elimination of [V | I] in `work`
+// ((2 R^2 + 6 R) double-floats).  Step j touches only the R columns
+// j+1 .. R+j (earlier left columns are finished unit vectors, later right
+// columns are still identity columns) and reads row j and column j from side
+// buffers written by step j - 1, so every entry updates in place with one
+// barrier per step.  Returns false (on every thread) when a pivot is not
+// positive.
+__device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* Vs, df* Vis, df* work) {
   const int R2 = 2 * R;
-  df* M = reinterpret_cast<df*>(smraw);  // [V | I], row-major: M[i * 2R + c]
-  df* colb = M + R * R2;                 // column j of M, two buffers of R
-  df* rowb = colb + 2 * R;               // row j of M, two buffers of 2R
+  df* M = work;            // [V | I], row-major: M[i * 2R + c]
+  df* colb = M + R * R2;   // column j of M, two buffers of R
+  df* rowb = colb + 2 * R; // row j of M, two buffers of 2R
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int t = tid; t < R * R; t += nt) {
@@ -91,7 +90,7 @@ __global__ void __launch_bounds__(kInvThreads) als_inverse_df_kernel(const df* g
     for (int m = 0; m < kMaxOrder; ++m)
       if (m < N && m != n) v = df_mul(v, g[m]);
     const int i = t % R, c = t / R;  // V is symmetric: V[i][c]
-    V[t] = v;
+    Vs[t] = v;
     M[i * R2 + c] = v;
     M[i * R2 + R + c] = df_make(i == c ? 1.f : 0.f);
     if (c == 0) colb[i] = v;  // column 0 for step 0
@@ -102,17 +101,13 @@ __global__ void __launch_bounds__(kInvThreads) als_inverse_df_kernel(const df* g
   for (int j = tid; j < R; j += nt) rowb[(j & 1) * R2 + R + j] = df_make(1.f);
   __syncthreads();
 
-  bool fail = false;
   for (int j = 0; j < R; ++j) {
     const df* col = colb + (j & 1) * R;
     const df* row = rowb + (j & 1) * R2;
     df* coln = colb + ((j + 1) & 1) * R;
     df* rown = rowb + ((j + 1) & 1) * R2;
     const df p = col[j];
-    if (!(p.hi > 0.f)) {  // every thread read the same pivot
-      fail = true;
-      break;
-    }
+    if (!(p.hi > 0.f)) return false;  // every thread read the same pivot
     const df inv = df_rcp(p);
     for (int e = tid; e < R * R; e += nt) {
       const int i = e / R, c = j + 1 + (e - i * R);
@@ -123,27 +118,26 @@ __global__ void __launch_bounds__(kInvThreads) als_inverse_df_kernel(const df* g
     }
     __syncthreads();
   }
-  if (fail) {
-    if (tid == 0) {
-      atomicCAS(status, 0, int(CPG_ERR_SINGULAR));
-      Vi[0] = df{0.f, 0.f};
-    }
-    return;
-  }
   for (int t = tid; t < R * R; t += nt) {
     const int p = t % R, q = t / R;
-    Vi[t] = M[p * R2 + R + q];
+    Vis[t] = M[p * R2 + R + q];
   }
+  __syncthreads();
+  return true;
 }
 
-// ---- the update of one mode given V^{-1} -------------------------------------------
-constexpr int kAlsThreads = 1024;
+// ---- the update of one mode, by one block ---------------------------------------
+constexpr int kModeThreads = 512;
 
+// Shared memory of the update (V^{-1}, V, Gram_n, lambda, partials; then X
+// (double-float), G and the new factor (floats), all In x (R + 1)) and of the
+// inverse ([V | I], V, V^{-1} and the pivot row/column buffers); the mode
+// kernel takes the larger.
 inline size_t als_df_smem_bytes(int64_t In, int R) {
   const size_t RS = size_t(R) + 1, R2 = size_t(R) * R;
-  // V^{-1}, V, Gram_n, lambda, partials; X (df), then G and the new factor
-  // (floats), all In x RS.
-  return (3 * R2 + 2 * size_t(R)) * sizeof(df) + size_t(In) * RS * (sizeof(df) + 2 * sizeof(float)) + 16;
+  const size_t update = (3 * R2 + 2 * size_t(R)) * sizeof(df) + size_t(In) * RS * (sizeof(df) + 2 * sizeof(float));
+  const size_t inverse = (4 * R2 + 6 * size_t(R)) * sizeof(df);
+  return (update > inverse ? update : inverse) + 16;
 }
 
 __device__ __forceinline__ df df_warp_sum(df v) {
@@ -152,16 +146,14 @@ __device__ __forceinline__ df df_warp_sum(df v) {
   return v;
 }
 
-// One block of kAlsThreads threads.  Shared memory: als_df_smem_bytes(In, R).
 // Phases (each a short dependent chain, all entries in parallel):
-//   load     G, V^{-1}, V;
+//   load     V^{-1}, V (from the inverse CTA), G;
 //   X        = G V^{-1}, one output per thread;
 //   lambda   warp per column; a_q = x_q / lambda_q;
 //   Gram_n   8 lanes per (p, q) pair;
 //   fit      <Y, Yhat> = sum_q lambda_q <a_q, g_q>,
 //            ||Yhat||^2 = lambda^T (V * Gram_n) lambda.
-__global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
   const int R = a.R, n = a.n, RS = R + 1;
   const int In = int(a.In);  // In * (R + 1) fits the shared-memory budget, far below 2^31
   df* Vis = reinterpret_cast<df*>(smraw);    // V^{-1}[p][q] at p + R q
@@ -175,16 +167,19 @@ __global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfA
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const bool want_fit = a.fit_out != nullptr;
 
-  if (!(a.Vi[0].hi != 0.f)) return;  // V was not positive definite: leave this mode untouched
+  // Written by other CTAs of this launch: read through L2.
+  for (int t = tid; t < R * R; t += nt) {
+    const float2 vi = __ldcg(reinterpret_cast<const float2*>(a.Vi) + t);
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(a.V) + t);
+    Vis[t] = df{vi.x, vi.y};
+    Vs[t] = df{v.x, v.y};
+  }
   for (int t = tid; t < In * R; t += nt) {
     const int q = t / In, i = t - q * In;
-    Gs[i * RS + q] = a.G[t];
-  }
-  for (int t = tid; t < R * R; t += nt) {
-    Vis[t] = a.Vi[t];
-    Vs[t] = a.V[t];
+    Gs[i * RS + q] = __ldcg(a.G + t);
   }
   __syncthreads();
+  if (!(Vis[0].hi != 0.f)) return;  // V was not positive definite: leave this mode untouched
 
   // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], one output per thread.
   for (int t = tid; t < In * R; t += nt) {
@@ -287,6 +282,49 @@ __global__ void __launch_bounds__(kAlsThreads) als_update_df_kernel(const AlsDfA
       *a.fit_out = 1.0 - df_to_double(ratio);
     }
   }
+}
+
+// ---- one mode: G, then the update -------------------------------------------------
+struct AlsModeArgs {
+  SegDot<float> sd;        // produces G (sd.out == u.G): a finishing contraction or a recursion
+  AlsDfArgs u;             // the update of mode u.n
+  unsigned int* ticket;    // zero on entry; the last CTA resets it
+};
+
+// grid = (CTAs of the segmented dot) + 1 of kModeThreads threads, dynamic
+// shared memory als_df_smem_bytes(In, R).  LPO = lanes per output of the
+// segmented dot, or 0 for its tiled form (chain.cuh); the last CTA of the
+// grid forms V and V^{-1}.
+template <int LPO>
+__global__ void __launch_bounds__(kModeThreads) als_mode_df_kernel(const AlsModeArgs p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned int s_ticket;
+  if (blockIdx.x == gridDim.x - 1) {
+    const AlsDfArgs& u = p.u;
+    const int R = u.R;
+    df* Vs = reinterpret_cast<df*>(smraw);
+    df* Vis = Vs + R * R;
+    const bool ok = df_inverse_block(u.grams, u.N, u.n, R, Vs, Vis, Vis + R * R);
+    for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+      u.V[t] = Vs[t];
+      u.Vi[t] = ok ? Vis[t] : df{0.f, 0.f};
+    }
+    if (!ok && threadIdx.x == 0) atomicCAS(u.status, 0, int(CPG_ERR_SINGULAR));
+  } else if constexpr (LPO == 0) {
+    seg_dot_tiled_run<float>(p.sd, blockIdx.x);
+  } else {
+    seg_dot_run<float, LPO>(p.sd, blockIdx.x * int64_t(blockDim.x) + threadIdx.x);
+  }
+  // Publish this CTA's outputs, then take a ticket: the CTA with the last
+  // ticket sees every other CTA's outputs and runs the update.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(p.ticket, 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  if (threadIdx.x == 0) *p.ticket = 0u;  // ready for the next launch on this stream
+  als_update_block(p.u, smraw);
 }
 
 }  // namespace cpg

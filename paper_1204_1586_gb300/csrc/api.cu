@@ -22,10 +22,12 @@ namespace {
 
 thread_local uint64_t g_launches = 0;
 
-// Optional timing of leading-pass launches: CUDA events recorded on the launch
-// stream around every leading-contraction kernel while enabled.
+// Optional timing of launches: CUDA events recorded on the launch stream
+// around every leading-contraction kernel (mode 1) or every kernel (mode 2)
+// while enabled; each record keeps the launch's kind (cpgrad.h).
 struct LeadTiming {
   bool on = false;
+  bool all = false;
   int n = 0;
   static constexpr int kMax = 4096;
   cudaEvent_t ev[2 * kMax] = {};
@@ -33,6 +35,41 @@ struct LeadTiming {
   bool made = false;
 };
 LeadTiming g_timing;
+
+// Kinds of timed launches: 1-3 leading passes (sides), 10+ the rest.
+enum LaunchKind : int {
+  kKindChain = 10,   // finishing contraction or recursion (segmented dot)
+  kKindMode = 11,    // fused ALS mode: G, then the update (FP32 data)
+  kKindGram = 12,    // Gram matrices of all factors
+  kKindKron = 13,    // Kronecker vector of a run of modes
+  kKindNorm = 14,    // ||Y||^2 from partial sums
+  kKindUpdate = 15   // ALS update (FP64 data)
+};
+
+// Records a start event at construction and an end event at destruction when
+// timing is on for this kind of launch.
+class Timed {
+ public:
+  Timed(cudaStream_t st, int kind) : st_(st), kind_(kind) {
+    if (g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax && (kind < kKindChain || g_timing.all)) {
+      slot_ = g_timing.n++;
+      cudaEventRecord(g_timing.ev[2 * slot_], st_);
+    }
+  }
+  ~Timed() {
+    if (slot_ >= 0) {
+      cudaEventRecord(g_timing.ev[2 * slot_ + 1], st_);
+      g_timing.sides[slot_] = kind_;
+    }
+  }
+  Timed(const Timed&) = delete;
+  Timed& operator=(const Timed&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int kind_;
+  int slot_ = -1;
+};
 // Device status word of the current call's workspace (for kernels that report timeouts).
 thread_local int* g_status_ptr = nullptr;
 
@@ -274,9 +311,12 @@ struct Carver {
   }
 };
 
+// First kAlign bytes of every workspace: the device status word, ||Y||^2,
+// and the CTA ticket of the fused ALS mode kernels.
 struct Header {
   int* status;
   double* normY2;
+  unsigned int* ticket;
 };
 
 Header take_header(Carver& c) {
@@ -284,6 +324,7 @@ Header take_header(Carver& c) {
   char* p = c.take<char>(kAlign);
   h.status = reinterpret_cast<int*>(p);
   h.normY2 = p ? reinterpret_cast<double*>(p + 8) : nullptr;
+  h.ticket = p ? reinterpret_cast<unsigned int*>(p + 16) : nullptr;
   return h;
 }
 
@@ -361,8 +402,13 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
 
 // Fused pass unless its J-block partials would cost more than a fifth of Y's
 // bytes; then the two sides run as separate passes (the L pass with tall blocks).
+// The CUDA-core kernels fuse only at rank <= 4: with both sides a lane carries
+// 2R products per element and too many accumulators for two CTAs per SM (at
+// 100^4, R = 10 the fused pass ran at 2.0 TB/s against 5.1 and 4.2 TB/s for
+// the single sides).
 bool use_fused(const Shape& s, int R, int k, int prec) {
   if (prec == CPG_TF32X3) return false;  // the split-TF32 kernel runs one side per pass
+  if (!is_tc_prec(prec) && R > 4) return false;
   const LeadPlan f = plan_lead(s, R, k, 3, prec);
   return double(f.lpart_elems + f.rpart_elems) <= 0.2 * double(s.total);
 }
@@ -412,8 +458,8 @@ struct AlsWs {
   double* X;
   T* G;
   LeadTabs<T> tabs;
-  double* Vinv;  // [N][R][R] V^{-1} per mode (double-float pairs for FP32 data)
-  double* Vm;    // [N][R][R] V per mode
+  double* V;   // [R][R] V of the current mode (double-float pairs for FP32 data)
+  double* Vi;  // [R][R] V^{-1}
 };
 
 template <typename T>
@@ -431,41 +477,14 @@ AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const 
   w.X = c.take<double>(size_t(imax) * R);
   w.G = c.take<T>(size_t(imax) * R);
   w.tabs = take_tabs<T>(c, s, R, lr.k);
-  w.Vinv = c.take<double>(size_t(s.N) * R * R);
-  w.Vm = c.take<double>(size_t(s.N) * R * R);
+  w.V = c.take<double>(size_t(R) * R);
+  w.Vi = c.take<double>(size_t(R) * R);
   if (bytes) *bytes = c.off;
   return w;
 }
 
-// A second stream per device for work that depends only on small R x R
-// quantities (the normal-equation inverses of fast CP_ALS), so that it runs
-// while the main stream streams Y or contracts partial sums; ordered with the
-// main stream by events only.  Created once per device and kept.
-struct SideStream {
-  cudaStream_t stream = nullptr;
-  cudaEvent_t fork = nullptr;                // main -> side
-  cudaEvent_t done[kMaxOrder] = {};          // side -> main, one per mode
-};
-
-// Streams of a device's pool for batched calls (slot 0 of the side streams
-// serves single calls, slot 1 + i the pool's stream i).
+// Streams of a device's pool for batched calls.
 constexpr int kPoolStreams = 16;
-
-SideStream* side_stream(int slot = 0) {
-  static SideStream table[64][kPoolStreams + 1];
-  static std::mutex mu;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || slot < 0 || slot > kPoolStreams) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  SideStream& ss = table[dev][slot];
-  if (ss.stream == nullptr) {
-    if (cudaStreamCreateWithFlags(&ss.stream, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-    for (auto& e : ss.done)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-  }
-  return &ss;
-}
 
 inline int blocks_for(int64_t n, int threads, int cap = 4 * 1024) {
   int64_t b = (n + threads - 1) / threads;
@@ -490,6 +509,7 @@ const T* kr_vector(const Shape& s, const void* const* A, int R, int mb, int me, 
   if (me - mb == 1) return static_cast<const T*>(A[mb]);
   const int64_t len = prod(s, mb, me);
   ++g_launches;
+  Timed timer(st, kKindKron);
   kr_build_kernel<T><<<blocks_for(len * R, 256), 256, 0, st>>>(scratch, fac_args<T>(s, A), mb, me, len, R);
   return scratch;
 }
@@ -498,18 +518,9 @@ const T* kr_vector(const Shape& s, const void* const* A, int R, int mb, int me, 
 template <typename T>
 cudaError_t launch_lead(const LeadArgs<T>& a, int RT, int sides, dim3 g, cudaStream_t st) {
   ++g_launches;
-  const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
-  const int slot = g_timing.n;
-  if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
-  cudaError_t e;
-  if constexpr (sizeof(T) == 8) e = launch_lead_f64(a, RT, sides, g, st);
-  else e = launch_lead_f32(a, RT, sides, g, st);
-  if (timed) {
-    cudaEventRecord(g_timing.ev[2 * slot + 1], st);
-    g_timing.sides[slot] = sides;
-    g_timing.n = slot + 1;
-  }
-  return e;
+  Timed timer(st, sides);
+  if constexpr (sizeof(T) == 8) return launch_lead_f64(a, RT, sides, g, st);
+  else return launch_lead_f32(a, RT, sides, g, st);
 }
 
 // Khatri-Rao rows over modes [mb, me) as factor row x Kronecker-table entry.
@@ -544,14 +555,10 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
         a.r0 = g * p.RTmax;
         a.normpart = (g == 0) ? normpart : nullptr;
         ++g_launches;
-        const bool timed = g_timing.on && g_timing.made && g_timing.n < LeadTiming::kMax;
-        const int slot = g_timing.n;
-        if (timed) cudaEventRecord(g_timing.ev[2 * slot], st);
-        cudaError_t e = launch_lead_tc(Y, a, p.RTP, p.sides, p.tc_prec, dim3(p.nJb, p.nKs), st);
-        if (timed) {
-          cudaEventRecord(g_timing.ev[2 * slot + 1], st);
-          g_timing.sides[slot] = p.sides;
-          g_timing.n = slot + 1;
+        cudaError_t e;
+        {
+          Timed timer(st, p.sides);
+          e = launch_lead_tc(Y, a, p.RTP, p.sides, p.tc_prec, dim3(p.nJb, p.nKs), st);
         }
         if (e != cudaSuccess) return e;
       }
@@ -581,26 +588,36 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   return cudaSuccess;
 }
 
+// Lanes per output of a segmented dot product of reduction length `inner`.
+inline int seg_lanes(int64_t inner) { return inner >= 96 ? 32 : inner >= 24 ? 8 : inner >= 4 ? 4 : 1; }
+
 template <typename T>
 void launch_seg(const SegDot<T>& p, cudaStream_t st) {
   ++g_launches;
+  Timed timer(st, kKindChain);
   const int64_t nout = p.D * p.R;
   auto go = [&](auto kern, int lpo) {
     const int64_t threads = nout * lpo;
     const int blocks = int(std::max<int64_t>(1, (threads + 255) / 256));
     kern<<<blocks, 256, 0, st>>>(p);
   };
-  if (p.inner >= 96) go(seg_dot_kernel<T, 32>, 32);
-  else if (p.inner >= 24) go(seg_dot_kernel<T, 8>, 8);
-  else if (p.inner >= 4) go(seg_dot_kernel<T, 4>, 4);
-  else go(seg_dot_kernel<T, 1>, 1);
+  if (seg_use_tiled(p)) {
+    seg_dot_tiled_kernel<T><<<int(seg_tiled_blocks(p)), kSegWarps * 32, 0, st>>>(p);
+    return;
+  }
+  switch (seg_lanes(p.inner)) {
+    case 32: go(seg_dot_kernel<T, 32>, 32); break;
+    case 8: go(seg_dot_kernel<T, 8>, 8); break;
+    case 4: go(seg_dot_kernel<T, 4>, 4); break;
+    default: go(seg_dot_kernel<T, 1>, 1); break;
+  }
 }
 
 // Finishing contraction for mode i of X (RIGHT: flat = o + len_o*i, LEFT: flat = i + In*o):
 // G[i + In r] = sum_o X[r][flat] kr[r][o].
 template <typename T, bool RIGHT>
-void launch_grad(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, int R, const T* kr, T* G, T* Xred,
-                 cudaStream_t st) {
+SegDot<T> grad_seg(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, int R, const T* kr, T* G,
+                   T* Xred) {
   SegDot<T> p{};
   p.X = X;
   p.nparts = nparts;
@@ -615,12 +632,18 @@ void launch_grad(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t
   p.out = G;
   p.Xred = (nparts > 1) ? Xred : nullptr;
   p.R = R;
-  launch_seg(p, st);
+  return p;
+}
+
+template <typename T, bool RIGHT>
+void launch_grad(const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, int R, const T* kr, T* G, T* Xred,
+                 cudaStream_t st) {
+  launch_seg(grad_seg<T, RIGHT>(X, nparts, pstride, len_o, In, R, kr, G, Xred), st);
 }
 
 // Recursion over mode i of X: Xout[r][o] = sum_i X[r][flat] A[i + In r].
 template <typename T, bool RIGHT>
-void launch_contract(const T* X, int64_t len_o, int64_t In, int R, const T* An, T* Xout, cudaStream_t st) {
+SegDot<T> contract_seg(const T* X, int64_t len_o, int64_t In, int R, const T* An, T* Xout) {
   SegDot<T> p{};
   p.X = X;
   p.nparts = 1;
@@ -635,7 +658,38 @@ void launch_contract(const T* X, int64_t len_o, int64_t In, int R, const T* An, 
   p.out = Xout;
   p.Xred = nullptr;
   p.R = R;
-  launch_seg(p, st);
+  return p;
+}
+
+template <typename T, bool RIGHT>
+void launch_contract(const T* X, int64_t len_o, int64_t In, int R, const T* An, T* Xout, cudaStream_t st) {
+  launch_seg(contract_seg<T, RIGHT>(X, len_o, In, R, An, Xout), st);
+}
+
+// One fused ALS mode (FP32 data): the segmented dot that produces G, then
+// the update of mode u.n by the CTA that finishes last.
+void launch_mode_update(const SegDot<float>& sd, const AlsDfArgs& u, unsigned int* ticket, cudaStream_t st) {
+  ++g_launches;
+  Timed timer(st, kKindMode);
+  AlsModeArgs p{sd, u, ticket};
+  const bool tiled = seg_use_tiled(sd);
+  static_assert(kModeThreads == kSegWarps * 32, "the tiled segmented dot runs on mode-kernel blocks");
+  const int lpo = tiled ? 0 : seg_lanes(sd.inner);
+  const int64_t threads = sd.D * sd.R * std::max(lpo, 1);
+  const int64_t seg_blocks = tiled ? seg_tiled_blocks(sd) : std::max<int64_t>(1, (threads + kModeThreads - 1) / kModeThreads);
+  const int blocks = int(seg_blocks + 1);  // + the inverse CTA
+  const size_t smem = als_df_smem_bytes(u.In, u.R);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    kern<<<blocks, kModeThreads, smem, st>>>(p);
+  };
+  switch (lpo) {
+    case 0: go(als_mode_df_kernel<0>); break;
+    case 32: go(als_mode_df_kernel<32>); break;
+    case 8: go(als_mode_df_kernel<8>); break;
+    case 4: go(als_mode_df_kernel<4>); break;
+    default: go(als_mode_df_kernel<1>); break;
+  }
 }
 
 cpg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPG_OK : CPG_ERR_CUDA; }
@@ -758,7 +812,7 @@ constexpr int kAlsMaxRank = 64;
 
 template <typename T>
 cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, int R, int iters, double* fit,
-                    const cpg_opts* o, int* status_override = nullptr, int side_slot = 0) {
+                    const cpg_opts* o, int* status_override = nullptr) {
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
   if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
   const int k = choose_split(s, o);
@@ -773,68 +827,36 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   const void* const* Ac = const_cast<const void* const*>(A);
 
   constexpr bool kDf = std::is_same_v<T, float>;
-  ++g_launches;
-  if constexpr (kDf)
-    gram_all_df_kernel<<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R,
-                                                                                    reinterpret_cast<df*>(w.grams));
-  else
-    gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
-  const size_t upd_smem = size_t(3) * R * R * sizeof(double);
   int64_t imax = 1;
   for (int m = 0; m < s.N; ++m) imax = std::max(imax, s.I[m]);
   constexpr size_t kSmemCap = 200 * 1024;
   const bool smem_path = (kDf ? als_df_smem_bytes(imax, R) : als_smem_bytes(imax, R)) <= kSmemCap;
-  SideStream* side = nullptr;
-  if constexpr (kDf) {
-    if (!smem_path) return CPG_ERR_UNSUPPORTED;
-    cudaFuncSetAttribute(als_update_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(als_df_smem_bytes(imax, R)));
-    cudaFuncSetAttribute(als_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(als_inv_smem_bytes(R)));
-    side = side_stream(side_slot);
-    if (side == nullptr) return CPG_ERR_CUDA;
-  } else {
+  if (kDf && !smem_path) return CPG_ERR_UNSUPPORTED;
+  const size_t upd_smem = size_t(3) * R * R * sizeof(double);
+  if constexpr (!kDf) {
     cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
     if (smem_path)
       cudaFuncSetAttribute(als_update_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(als_smem_bytes(imax, R)));
+  } else {
+    // The fused mode kernels' CTA ticket starts at zero.
+    if (cudaMemsetAsync(w.h.ticket, 0, sizeof(unsigned int), st) != cudaSuccess) return CPG_ERR_CUDA;
   }
 
-  // Finishing contraction of mode m into w.G, or nothing when it is the
-  // identity: a single remaining mode with no partial sums to add leaves
-  // X[r][i] = G[i + In r], so the update reads X itself.
-  auto finish = [&](auto right_tag, const T* X, int nparts, int64_t pstride, int64_t len_o, int64_t In, const T* kr,
-                    T* Xred) -> const T* {
-    constexpr bool RIGHT = decltype(right_tag)::value;
-    if (len_o == 1 && nparts == 1) return X;
-    launch_grad<T, RIGHT>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred, st);
-    return w.G;
-  };
-  // Update order of one sweep (Section 4): k-1, ..., 0, then k, ..., N-1.
-  std::vector<int> order;
-  for (int m = k - 1; m >= 0; --m) order.push_back(m);
-  for (int m = k; m < s.N; ++m) order.push_back(m);
-  const int64_t total_updates = int64_t(iters) * s.N;
-  int64_t upd = 0;  // updates issued so far
-  df* const Vi_all = reinterpret_cast<df*>(w.Vinv);
-  df* const V_all = reinterpret_cast<df*>(w.Vm);
-  // V and V^{-1} of mode n on the side stream, after everything issued so far
-  // on the main stream (the Grams it reads are then final).
-  auto fork_inverse = [&](int n) {
-    if constexpr (kDf) {
-      cudaEventRecord(side->fork, st);
-      cudaStreamWaitEvent(side->stream, side->fork, 0);
-      ++g_launches;
-      als_inverse_df_kernel<<<1, kInvThreads, als_inv_smem_bytes(R), side->stream>>>(
-          reinterpret_cast<const df*>(w.grams), s.N, n, R, V_all + int64_t(n) * R * R, Vi_all + int64_t(n) * R * R,
-          w.h.status);
-      cudaEventRecord(side->done[n], side->stream);
-    }
-  };
-  if constexpr (kDf) fork_inverse(order[0]);
+  ++g_launches;
+  if constexpr (kDf) {
+    Timed timer(st, kKindGram);
+    gram_all_df_kernel<<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R,
+                                                                                    reinterpret_cast<df*>(w.grams));
+  } else {
+    Timed timer(st, kKindGram);
+    gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
+  }
 
-  auto update = [&](int n, const T* Gn, double* fit_out) {
-    ++g_launches;
+  // The update of mode n from G^(n) = Gn.  FP32 data: fused into the kernel
+  // that produces G (sd, whose output is w.G); FP64 data: its own launch
+  // after the G kernel.
+  auto update = [&](int n, const SegDot<T>& sd, double* fit_out) {
     if constexpr (kDf) {
       AlsDfArgs u{};
       u.N = s.N;
@@ -842,26 +864,27 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.R = R;
       u.In = s.I[n];
       u.grams = reinterpret_cast<df*>(w.grams);
-      u.Vi = Vi_all + int64_t(n) * R * R;
-      u.V = V_all + int64_t(n) * R * R;
-      u.G = Gn;
+      u.V = reinterpret_cast<df*>(w.V);
+      u.Vi = reinterpret_cast<df*>(w.Vi);
+      u.G = sd.out;
       u.An = static_cast<float*>(A[n]);
       u.lambda = lambda;
       u.status = w.h.status;
       u.fit_out = fit_out;
       u.normY2 = w.h.normY2;
-      cudaStreamWaitEvent(st, side->done[n], 0);
-      als_update_df_kernel<<<1, kAlsThreads, als_df_smem_bytes(s.I[n], R), st>>>(u);
-      // The next update's inverse needs this mode's new Gram: fork it now.
-      if (++upd < total_updates) fork_inverse(order[upd % s.N]);
+      launch_mode_update(sd, u, w.h.ticket, st);
     } else {
+      const bool identity = sd.inner == 1 && sd.nparts == 1 && sd.X == sd.out;
+      if (!identity) launch_seg(sd, st);
+      ++g_launches;
+      Timed timer(st, kKindUpdate);
       AlsArgs<T> u{};
       u.N = s.N;
       u.n = n;
       u.R = R;
       u.In = s.I[n];
       u.grams = w.grams;
-      u.G = Gn;
+      u.G = sd.out;
       u.An = static_cast<T*>(A[n]);
       u.lambda = lambda;
       u.X = w.X;
@@ -874,13 +897,30 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
         als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
     }
   };
+  // G^(n) of a mode whose finishing contraction is the identity (a single
+  // remaining mode with no partial sums): X itself.  FP64 data reads it in
+  // place; FP32 data copies it into w.G inside the fused kernel.
+  auto identity_seg = [&](const T* X, int64_t In) {
+    SegDot<T> p{};
+    p.X = X;
+    p.nparts = 1;
+    p.S = In;
+    p.D = In;
+    p.astep = 1;
+    p.ustep = 1;
+    p.inner = 1;
+    p.out = kDf ? w.G : const_cast<T*>(X);
+    p.R = R;
+    return p;
+  };
 
   for (int it = 0; it < iters; ++it) {
-    // Pass 1: R^(k) with the current trailing factors (step 4).
+    // Pass 1: R^(k) with the current trailing factors (step 4); modes k-1, ..., 0.
     double* np = (it == 0) ? w.normpart : nullptr;
     if (run_lead<T>(s, Y, Ac, R, lr, w.Rpart, nullptr, np, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     if (it == 0) {
       ++g_launches;
+      Timed timer(st, kKindNorm);
       sum_norm_kernel<<<1, 256, 0, st>>>(w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
     }
     {
@@ -889,24 +929,39 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       const int64_t pstride = int64_t(R) * lr.J;
       T* bufs[2] = {w.ch.Pa, w.ch.Pb};
       int cur = 0;
+      bool g_done = false;  // this mode's update already ran (fused with the recursion)
       for (int n = k; n >= 1; --n) {
         const int m = n - 1;
         const int64_t len_o = prod(s, 0, m), In = s.I[m];
-        const T* kr = kr_vector<T>(s, Ac, R, 0, m, w.ch.kr, st);
-        T* Xred = (nparts > 1 && m > 0) ? bufs[cur] : nullptr;
-        const T* Gm = finish(std::true_type{}, X, nparts, pstride, len_o, In, kr, Xred);
-        update(m, Gm, nullptr);
+        T* Xred = nullptr;
+        if (!g_done) {
+          if (len_o == 1 && nparts == 1) {
+            update(m, identity_seg(X, In), nullptr);
+          } else {
+            const T* kr = kr_vector<T>(s, Ac, R, 0, m, w.ch.kr, st);
+            Xred = (nparts > 1 && m > 0) ? bufs[cur] : nullptr;
+            update(m, grad_seg<T, true>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred), nullptr);
+          }
+        }
+        g_done = false;
         if (m > 0) {
+          // Recursion with the updated a^(m) (eq. 3.20).  When the next mode is
+          // mode 0, the contracted tensor is G^(0) itself: its update is fused.
           const T* src = Xred ? Xred : X;
-          T* dst = bufs[cur ^ 1];
-          launch_contract<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), dst, st);
-          X = dst;
-          nparts = 1;
-          cur ^= 1;
+          if (kDf && m == 1) {
+            update(0, contract_seg<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), w.G), nullptr);
+            g_done = true;
+          } else {
+            T* dst = bufs[cur ^ 1];
+            launch_contract<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), dst, st);
+            X = dst;
+            nparts = 1;
+            cur ^= 1;
+          }
         }
       }
     }
-    // Pass 2: L^(k+1) with the updated leading factors (step 7).
+    // Pass 2: L^(k+1) with the updated leading factors (step 7); modes k, ..., N-1.
     if (run_lead<T>(s, Y, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
     {
       const T* X = w.Lpart;
@@ -914,19 +969,35 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       const int64_t pstride = int64_t(R) * ll.K;
       T* bufs[2] = {w.ch.Qa, w.ch.Qb};
       int cur = 0;
+      bool g_done = false;
+      auto fit_of = [&](int n) { return (n == s.N - 1 && fit) ? fit + it : nullptr; };
       for (int n = k; n < s.N; ++n) {
         const int64_t len_o = prod(s, n + 1, s.N), In = s.I[n];
-        const T* kr = kr_vector<T>(s, Ac, R, n + 1, s.N, w.ch.kr, st);
-        T* Xred = (nparts > 1 && n < s.N - 1) ? bufs[cur] : nullptr;
-        const T* Gn = finish(std::false_type{}, X, nparts, pstride, len_o, In, kr, Xred);
-        update(n, Gn, (n == s.N - 1 && fit) ? fit + it : nullptr);
+        T* Xred = nullptr;
+        if (!g_done) {
+          if (len_o == 1 && nparts == 1) {
+            update(n, identity_seg(X, In), fit_of(n));
+          } else {
+            const T* kr = kr_vector<T>(s, Ac, R, n + 1, s.N, w.ch.kr, st);
+            Xred = (nparts > 1 && n < s.N - 1) ? bufs[cur] : nullptr;
+            update(n, grad_seg<T, false>(X, nparts, pstride, len_o, In, R, kr, w.G, Xred), fit_of(n));
+          }
+        }
+        g_done = false;
         if (n < s.N - 1) {
+          // Recursion with the updated a^(n) (eq. 3.22); fused with the update
+          // of mode N-1 when that is the next mode.
           const T* src = Xred ? Xred : X;
-          T* dst = bufs[cur ^ 1];
-          launch_contract<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), dst, st);
-          X = dst;
-          nparts = 1;
-          cur ^= 1;
+          if (kDf && n + 1 == s.N - 1) {
+            update(n + 1, contract_seg<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), w.G), fit_of(n + 1));
+            g_done = true;
+          } else {
+            T* dst = bufs[cur ^ 1];
+            launch_contract<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), dst, st);
+            X = dst;
+            nparts = 1;
+            cur ^= 1;
+          }
         }
       }
     }
@@ -1084,6 +1155,7 @@ int cpg_profile_lead(int enable) {
     g_timing.made = true;
   }
   g_timing.on = enable != 0;
+  g_timing.all = enable == 2;
   g_timing.n = 0;
   return CPG_OK;
 }
@@ -1166,9 +1238,8 @@ cpg_status cp_als_batched(int B, const cpg_tensor_desc* descs, int iters, const 
     const cpg_status st =
         is_f64(opts->precision)
             ? als_impl<double>(shapes[b], static_cast<const double*>(d.Y), d.A, d.lambda, d.R, iters, d.fit, &mo,
-                               status, 1 + i)
-            : als_impl<float>(shapes[b], static_cast<const float*>(d.Y), d.A, d.lambda, d.R, iters, d.fit, &mo, status,
-                              1 + i);
+                               status)
+            : als_impl<float>(shapes[b], static_cast<const float*>(d.Y), d.A, d.lambda, d.R, iters, d.fit, &mo, status);
     if (st != CPG_OK) {
       result = st;
       break;

@@ -60,10 +60,10 @@ struct SegDot {
 // LPO lanes cooperate on one output; lanes stride the reduction index.  The
 // partial sums of an element are loaded in batches of 8 ahead of their
 // additions (which keep the fixed order q = 0, 1, ...), so that the loads
-// overlap instead of each waiting for the previous add.
+// overlap instead of each waiting for the previous add.  gid = global thread
+// index; every lane of a warp must call it (shuffle reduction).
 template <typename T, int LPO>
-__global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
-  const int64_t gid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__device__ __forceinline__ void seg_dot_run(const SegDot<T>& p, int64_t gid) {
   const int64_t t = gid / LPO;
   const int sub = int(gid % LPO);
   const int64_t nout = p.D * p.R;
@@ -103,6 +103,84 @@ __global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
     for (int s = LPO / 2; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s, LPO);
   }
   if (live && sub == 0) p.out[t] = acc;
+}
+
+template <typename T, int LPO>
+__global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
+  seg_dot_run<T, LPO>(p, blockIdx.x * int64_t(blockDim.x) + threadIdx.x);
+}
+
+// The same product when consecutive outputs are consecutive in X (astep == 1)
+// and the reduction index is strided (ustep > 1): lanes take 32 consecutive
+// outputs of one rank column, so every load of a warp is one contiguous run,
+// and the kSegWarps warps of a block take interleaved slices of the
+// reduction, summed through shared memory in a fixed order.  Block `blk` of
+// seg_tiled_blocks(p) covers outputs [32 g, 32 g + 32) of rank r, with
+// g = blk % groups and r = blk / groups.
+constexpr int kSegWarps = 16;
+
+template <typename T>
+inline int64_t seg_tiled_groups(const SegDot<T>& p) {
+  return (p.D + 31) / 32;
+}
+template <typename T>
+inline int64_t seg_tiled_blocks(const SegDot<T>& p) {
+  return seg_tiled_groups(p) * p.R;
+}
+
+template <typename T>
+__device__ __forceinline__ void seg_dot_tiled_run(const SegDot<T>& p, int64_t blk) {
+  __shared__ T red[kSegWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t groups = (p.D + 31) / 32;
+  const int r = int(blk / groups);
+  const int64_t a = (blk - int64_t(r) * groups) * 32 + lane;
+  const bool live = a < p.D;
+  const T* __restrict__ X = p.X;
+  const T* __restrict__ w = p.w ? p.w + int64_t(r) * p.wlen : nullptr;
+  const int nparts = p.nparts;
+  T acc = T(0);
+  if (live) {
+    const int64_t base = int64_t(r) * p.S + a;
+#pragma unroll 4
+    for (int64_t u = warp; u < p.inner; u += kSegWarps) {
+      const int64_t off = base + u * p.ustep;
+      T x;
+      if (nparts == 1) {
+        x = X[off];
+      } else {
+        x = T(0);
+        for (int q0 = 0; q0 < nparts; q0 += 8) {
+          T v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = (q0 + e < nparts) ? X[(q0 + e) * p.part_stride + off] : T(0);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x += v[e];
+        }
+        if (p.Xred) p.Xred[off] = x;
+      }
+      acc = w ? fma(x, w[u], acc) : acc + x;
+    }
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && live) {
+    T sum = T(0);
+#pragma unroll
+    for (int k = 0; k < kSegWarps; ++k) sum += red[k][lane];
+    p.out[a + p.D * r] = sum;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSegWarps * 32) seg_dot_tiled_kernel(const SegDot<T> p) {
+  seg_dot_tiled_run<T>(p, blockIdx.x);
+}
+
+// The tiled form when outputs are contiguous and the reduction is strided.
+template <typename T>
+inline bool seg_use_tiled(const SegDot<T>& p) {
+  return p.astep == 1 && p.ustep > 1 && p.inner >= 8;
 }
 
 }  // namespace cpg
