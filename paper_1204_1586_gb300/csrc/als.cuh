@@ -36,6 +36,7 @@ struct AlsArgs {
 // Gram matrices of all N factors (FP64).  grid = (ceil(R*R/256), N).
 template <typename T>
 __global__ void gram_all_kernel(const FacArgs<T> f, int R, double* grams) {
+  griddep_wait();
   const int m = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= R * R) return;
@@ -49,6 +50,7 @@ __global__ void gram_all_kernel(const FacArgs<T> f, int R, double* grams) {
 
 // Sum of the leading pass's per-CTA partial sums of y^2.  One block.
 __global__ void sum_norm_kernel(const double* part, int64_t n, double* out) {
+  griddep_wait();
   __shared__ double sh[32];
   double s = 0.0;
   for (int64_t t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
@@ -78,6 +80,7 @@ inline size_t als_smem_bytes(int64_t In, int R) {
 
 template <typename T>
 __global__ void __launch_bounds__(512) als_update_smem_kernel(const AlsArgs<T> a) {
+  griddep_wait();
   extern __shared__ __align__(16) double sm[];
   const int R = a.R, N = a.N, n = a.n, RS = R + 1;
   const int64_t In = a.In;
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(512) als_update_smem_kernel(const AlsArgs<T> a
 // One block of 256 threads.  Shared memory: 3 * R * R doubles.
 template <typename T>
 __global__ void __launch_bounds__(256) als_update_kernel(const AlsArgs<T> a) {
+  griddep_wait();
   extern __shared__ __align__(16) double sm[];
   const int R = a.R, N = a.N, n = a.n;
   const int64_t In = a.In;

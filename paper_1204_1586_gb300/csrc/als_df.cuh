@@ -53,6 +53,7 @@ struct AlsDfArgs {
 
 // Gram matrices of all N factors.  grid = (ceil(R*R/256), N).
 __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
+  griddep_wait();
   const int m = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= R * R) return;
@@ -299,6 +300,7 @@ template <int LPO>
 __global__ void __launch_bounds__(kModeThreads) als_mode_df_kernel(const AlsModeArgs p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ unsigned int s_ticket;
+  griddep_wait();
   if (blockIdx.x == gridDim.x - 1) {
     const AlsDfArgs& u = p.u;
     const int R = u.R;
@@ -324,6 +326,9 @@ __global__ void __launch_bounds__(kModeThreads) als_mode_df_kernel(const AlsMode
   if (s_ticket != gridDim.x - 1) return;
   __threadfence();
   if (threadIdx.x == 0) *p.ticket = 0u;  // ready for the next launch on this stream
+  // Every other CTA has exited: the next kernel may start launching (it waits
+  // for this one before reading anything this update writes).
+  griddep_launch();
   als_update_block(p.u, smraw);
 }
 

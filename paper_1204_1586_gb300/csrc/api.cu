@@ -510,7 +510,8 @@ const T* kr_vector(const Shape& s, const void* const* A, int R, int mb, int me, 
   const int64_t len = prod(s, mb, me);
   ++g_launches;
   Timed timer(st, kKindKron);
-  kr_build_kernel<T><<<blocks_for(len * R, 256), 256, 0, st>>>(scratch, fac_args<T>(s, A), mb, me, len, R);
+  launch_pdl(kr_build_kernel<T>, dim3(blocks_for(len * R, 256)), dim3(256), 0, st, scratch, fac_args<T>(s, A), mb, me,
+             len, R);
   return scratch;
 }
 
@@ -599,10 +600,10 @@ void launch_seg(const SegDot<T>& p, cudaStream_t st) {
   auto go = [&](auto kern, int lpo) {
     const int64_t threads = nout * lpo;
     const int blocks = int(std::max<int64_t>(1, (threads + 255) / 256));
-    kern<<<blocks, 256, 0, st>>>(p);
+    launch_pdl(kern, dim3(blocks), dim3(256), 0, st, p);
   };
   if (seg_use_tiled(p)) {
-    seg_dot_tiled_kernel<T><<<int(seg_tiled_blocks(p)), kSegWarps * 32, 0, st>>>(p);
+    launch_pdl(seg_dot_tiled_kernel<T>, dim3(int(seg_tiled_blocks(p))), dim3(kSegWarps * 32), 0, st, p);
     return;
   }
   switch (seg_lanes(p.inner)) {
@@ -681,7 +682,7 @@ void launch_mode_update(const SegDot<float>& sd, const AlsDfArgs& u, unsigned in
   const size_t smem = als_df_smem_bytes(u.In, u.R);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    kern<<<blocks, kModeThreads, smem, st>>>(p);
+    launch_pdl(kern, dim3(blocks), dim3(kModeThreads), smem, st, p);
   };
   switch (lpo) {
     case 0: go(als_mode_df_kernel<0>); break;
@@ -846,11 +847,12 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   ++g_launches;
   if constexpr (kDf) {
     Timed timer(st, kKindGram);
-    gram_all_df_kernel<<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R,
-                                                                                    reinterpret_cast<df*>(w.grams));
+    launch_pdl(gram_all_df_kernel, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac), R,
+               reinterpret_cast<df*>(w.grams));
   } else {
     Timed timer(st, kKindGram);
-    gram_all_kernel<T><<<dim3(blocks_for(int64_t(R) * R, 256), s.N), 256, 0, st>>>(fac_args<T>(s, Ac), R, w.grams);
+    launch_pdl(gram_all_kernel<T>, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac), R,
+               w.grams);
   }
 
   // The update of mode n from G^(n) = Gn.  FP32 data: fused into the kernel
@@ -892,9 +894,9 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       u.fit_out = fit_out;
       u.normY2 = w.h.normY2;
       if (smem_path)
-        als_update_smem_kernel<T><<<1, 512, als_smem_bytes(s.I[n], R), st>>>(u);
+        launch_pdl(als_update_smem_kernel<T>, dim3(1), dim3(512), als_smem_bytes(s.I[n], R), st, u);
       else
-        als_update_kernel<T><<<1, 256, upd_smem, st>>>(u);
+        launch_pdl(als_update_kernel<T>, dim3(1), dim3(256), upd_smem, st, u);
     }
   };
   // G^(n) of a mode whose finishing contraction is the identity (a single
@@ -921,7 +923,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     if (it == 0) {
       ++g_launches;
       Timed timer(st, kKindNorm);
-      sum_norm_kernel<<<1, 256, 0, st>>>(w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
+      launch_pdl(sum_norm_kernel, dim3(1), dim3(256), 0, st, w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
     }
     {
       const T* X = w.Rpart;

@@ -33,6 +33,7 @@ struct FacArgs {
 
 template <typename T>
 __global__ void kr_build_kernel(T* __restrict__ out, const FacArgs<T> f, int mb, int me, int64_t len, int R) {
+  griddep_wait();
   const int64_t total = len * R;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     const int r = int(t / len);
@@ -107,6 +108,7 @@ __device__ __forceinline__ void seg_dot_run(const SegDot<T>& p, int64_t gid) {
 
 template <typename T, int LPO>
 __global__ void __launch_bounds__(256) seg_dot_kernel(const SegDot<T> p) {
+  griddep_wait();
   seg_dot_run<T, LPO>(p, blockIdx.x * int64_t(blockDim.x) + threadIdx.x);
 }
 
@@ -174,6 +176,7 @@ __device__ __forceinline__ void seg_dot_tiled_run(const SegDot<T>& p, int64_t bl
 
 template <typename T>
 __global__ void __launch_bounds__(kSegWarps * 32) seg_dot_tiled_kernel(const SegDot<T> p) {
+  griddep_wait();
   seg_dot_tiled_run<T>(p, blockIdx.x);
 }
 

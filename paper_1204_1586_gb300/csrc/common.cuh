@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -83,6 +84,33 @@ struct LeadArgs {
   int use_tma;              // 1: tiles arrive by TMA (set by the launcher); 0: element copies
   int* status;              // device status word (bounded-wait timeouts)
 };
+
+// ---- programmatic dependent launch ----------------------------------------------
+// Kernels are launched with programmatic stream serialization (launch_pdl), so
+// a kernel may start while the previous kernel on its stream is finishing.
+// griddep_wait() blocks until that kernel has completed and its writes are
+// visible (a no-op after an ordinary launch); every kernel calls it before it
+// reads what an earlier kernel wrote or writes what one may still read.
+// griddep_launch() lets the next kernel start launching; a kernel that never
+// calls it triggers when all its CTAs have exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ---- cp.async (LDGSTS) wrappers ------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

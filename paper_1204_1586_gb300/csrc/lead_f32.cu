@@ -19,8 +19,7 @@ cudaError_t run(const LeadArgs<float>& a, dim3 grid, cudaStream_t st) {
                               CU_TENSOR_MAP_SWIZZLE_128B)
                   ? 1
                   : 0;
-  kern<<<grid, C::NT, C::smem_bytes, st>>>(m, b);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(C::NT), C::smem_bytes, st, m, b);
 }
 
 // TJ: row tile of the R-side and fused instances; TJL: of the L-side-only

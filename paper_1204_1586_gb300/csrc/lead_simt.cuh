@@ -323,6 +323,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     }
   };
   const bool wl_per_stage = DO_L && !DO_R && nrt > 1;
+  __syncthreads();  // barriers initialised
+  // The first stages read only Y, which no kernel writes: they are in flight
+  // before the previous kernel's results (the factors) are awaited.
+#pragma unroll 1
+  for (int s = 0; s < STAGES - 1; ++s) issue(s);
+  griddep_wait();
   if constexpr (DO_L) {
     fetch_wl(0);
     store_wl(WLs);
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     fetch_wr(0);
     store_wr(0);
   }
-  __syncthreads();  // barriers initialised, first Khatri-Rao rows stored
+  __syncthreads();  // first Khatri-Rao rows stored
 
   constexpr int NP = RT / 2;  // rank pairs (FP32)
   T racc[C::NLD][C::VECR][(DO_R && !C::F2) ? RT : 1];                          // FP64 accumulators
@@ -370,9 +376,6 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   // L-side lane placement.
   const int wr = warp % C::WR, wc = warp / C::WR;
   const int cl0 = wc * 32 * C::TCL + lane;
-
-#pragma unroll 1
-  for (int s = 0; s < STAGES - 1; ++s) issue(s);
 
   int ci = 0, rt = 0;  // column chunk and row tile of stage it
 #pragma unroll 1

@@ -20,8 +20,7 @@ cudaError_t run(const CUtensorMap& m, const TcArgs& a, dim3 grid, cudaStream_t s
   auto kern = lead_tc_kernel<RTP, SIDES, PREC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
   if (e != cudaSuccess) return e;
-  kern<<<grid, C::NT, C::smem_bytes, st>>>(m, a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(C::NT), C::smem_bytes, st, m, a);
 }
 
 template <int RTP, int PREC>

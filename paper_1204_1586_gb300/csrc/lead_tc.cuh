@@ -211,7 +211,10 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
       issue_copies(ss);
     }
   };
+  // The first super-stages read only Y, which no kernel writes: they are in
+  // flight before the previous kernel's results (the factors) are awaited.
   for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue(ss);
+  griddep_wait();
 
   // Khatri-Rao B tile: rows n < RTP are hi, rows RTP + n are lo (X3).  Lanes
   // take consecutive index pairs of one rank, so factor loads coalesce and

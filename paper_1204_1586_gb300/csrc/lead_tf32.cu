@@ -26,8 +26,7 @@ cudaError_t run(const TcArgs& a, dim3 grid, cudaStream_t st) {
   auto kern = lead_tf32_kernel<RTP, SIDES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
   if (e != cudaSuccess) return e;
-  kern<<<grid, C::NT, C::smem_bytes, st>>>(m, b);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(C::NT), C::smem_bytes, st, m, b);
 }
 
 template <int RTP>

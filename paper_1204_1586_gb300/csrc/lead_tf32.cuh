@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(256, 1) lead_tf32_kernel(const __grid_constant
       issue_copies(ss);
     }
   };
+  // The first super-stages read only Y, which no kernel writes: they are in
+  // flight before the previous kernel's results (the factors) are awaited.
   for (int ss = 0; ss < C::NB && ss < nss; ++ss) issue(ss);
+  griddep_wait();
 
   // Khatri-Rao B tile [W_hi ; W_lo] over KS contraction indices from `base`:
   // a task is 4 consecutive indices of one rank (one 16-byte chunk per part);
