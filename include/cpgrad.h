@@ -84,8 +84,14 @@ typedef struct {
   void* stream;           /* cudaStream_t; NULL = legacy default stream          */
 } cpg_opts;
 
-/* Which call a workspace is sized for. */
-typedef enum { CPG_CALL_GRADIENT_ALL = 0, CPG_CALL_GRADIENT_MODE = 1, CPG_CALL_ALS = 2 } cpg_call;
+/* Which call a workspace is sized for (CPG_CALL_GRADIENT_TUNE:
+ * cpg_autotune_gradient, the largest of its candidate plans). */
+typedef enum {
+  CPG_CALL_GRADIENT_ALL = 0,
+  CPG_CALL_GRADIENT_MODE = 1,
+  CPG_CALL_ALS = 2,
+  CPG_CALL_GRADIENT_TUNE = 3
+} cpg_call;
 
 /* n* = max{n : J_n <= K_n} of Algorithm 2 step 1, 1-based count of leading
  * modes, clamped into [1, N-1] (when I_1 > I_2...I_N no n qualifies and 1 is
@@ -103,6 +109,41 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
  * R^(n) and L^(n) (steps 11, 15, 19, 20).  G[n] are overwritten. */
 cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R,
                            void* const* G, const cpg_opts* opts);
+
+/* A plan of the all-mode gradient: the split k (number of leading modes in
+ * J, Algorithm 2 step 1) and whether steps 4 and 7 share one pass over Y. */
+typedef struct {
+  int split;       /* 1 <= split <= N-1                                   */
+  int fused;       /* 1: one pass computes steps 4 and 7; 0: two passes   */
+  float ms;        /* measured milliseconds per call (autotune only)      */
+  int candidates;  /* plans timed (autotune only)                         */
+} cpg_gradient_plan;
+
+/* Measured choice of the all-mode gradient's plan.  The paper picks the split
+ * n* by a cost model (Algorithm 2 step 1, Section 3.1); here every candidate
+ * is timed on the caller's data instead: each split k in [1, N-1] (or only
+ * opts->split when it is nonzero), as two single-side passes and, where the
+ * precision has one and its partial sums stay below the tensor's size, as one
+ * fused pass.  Each candidate runs once untimed, then `reps` times (1..1000)
+ * between CUDA events on opts->stream; the call synchronizes that stream, so
+ * it cannot be captured in a CUDA graph.  The fastest plan is recorded for
+ * this device, precision, requested split, rank and shape (process-wide,
+ * thread-safe) and written to *chosen (may be NULL).  G receives the gradient.
+ * Later cp_gradient_all / cp_gradient_all_noalloc calls with the same key run
+ * the recorded plan whenever their workspace holds it (cpg_workspace_size
+ * accounts for it), else the planner's.  Every plan computes the same
+ * gradient up to rounding.  The workspace must hold
+ * cpg_workspace_size(..., CPG_CALL_GRADIENT_TUNE) bytes, else
+ * CPG_ERR_WORKSPACE; argument errors as for cp_gradient_all. */
+cpg_status cpg_autotune_gradient(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                                 void* const* G, const cpg_opts* opts, int reps, cpg_gradient_plan* chosen);
+
+/* 1 and *plan (split, fused) when a measured plan is recorded for this shape,
+ * rank and opts (precision, split, current device); 0 otherwise.  Host-only. */
+int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_gradient_plan* plan);
+
+/* Forgets every recorded plan. */
+void cpg_autotune_clear(void);
 
 /* Single-mode CP gradient, Section 3.2: G^(n) via the right-to-left route
  * (eqs. 3.7, 3.10, 3.12) when J_n <= K_{n-1}, else the left-to-right route

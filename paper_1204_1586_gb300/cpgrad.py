@@ -22,10 +22,11 @@ LIB_PATH = os.path.join(_HERE, "libcpgrad.so")
 CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR_CUDA, CPG_ERR_TIMEOUT, \
     CPG_ERR_UNSUPPORTED = range(8)
 PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4}
-CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS = 0, 1, 2
+CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE = 0, 1, 2, 3
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
-           "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read"]
+           "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read", "cpg_autotune_gradient",
+           "cpg_gradient_plan_query", "cpg_autotune_clear"]
 
 
 class CpgError(RuntimeError):
@@ -37,6 +38,10 @@ class CpgError(RuntimeError):
 class cpg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("split", ctypes.c_int), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+class cpg_gradient_plan(ctypes.Structure):
+    _fields_ = [("split", ctypes.c_int), ("fused", ctypes.c_int), ("ms", ctypes.c_float), ("candidates", ctypes.c_int)]
 
 
 class cpg_tensor_desc(ctypes.Structure):
@@ -88,6 +93,14 @@ def lib() -> ctypes.CDLL:
         L.cpg_profile_lead.restype = ctypes.c_int
         L.cpg_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.cpg_profile_read.restype = ctypes.c_int
+        L.cpg_autotune_gradient.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, vpp,
+                                            ctypes.POINTER(cpg_opts), ctypes.c_int, ctypes.POINTER(cpg_gradient_plan)]
+        L.cpg_autotune_gradient.restype = ctypes.c_int
+        L.cpg_gradient_plan_query.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
+                                              ctypes.POINTER(cpg_gradient_plan)]
+        L.cpg_gradient_plan_query.restype = ctypes.c_int
+        L.cpg_autotune_clear.argtypes = []
+        L.cpg_autotune_clear.restype = None
         _lib = L
     return _lib
 
@@ -242,6 +255,46 @@ def cp_gradient_all(Y, I: Sequence[int], A, G=None, *, precision="fp32", split: 
     if st != CPG_OK:
         raise CpgError(st, "cp_gradient_all")
     return G
+
+
+def cp_gradient_autotune(Y, I: Sequence[int], A, G=None, *, precision="fp32", split: int = 0, reps: int = 3,
+                         workspace=None, stream=None):
+    """Times every plan of the all-mode gradient (split k, fused or two passes)
+    on these inputs and records the fastest for later cp_gradient_all calls of
+    this shape, rank and precision.  Returns {"split", "fused", "ms",
+    "candidates"}; G receives the gradient."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for n, a in enumerate(A):
+        _check_colmajor(a, int(I[n]), R, dtype, f"A[{n}]")
+    if G is None:
+        G = [torch.empty((R, int(In)), dtype=dtype, device=Y.device).t() for In in I]
+    for n, g in enumerate(G):
+        _check_colmajor(g, int(I[n]), R, dtype, f"G[{n}]")
+    sp = _stream_ptr(stream)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_GRADIENT_TUNE), sp)
+    plan = cpg_gradient_plan()
+    st = lib().cpg_autotune_gradient(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, _ptrs(G),
+                                     ctypes.byref(o), int(reps), ctypes.byref(plan))
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_autotune_gradient")
+    return {"split": plan.split, "fused": bool(plan.fused), "ms": float(plan.ms), "candidates": plan.candidates}
+
+
+def gradient_plan(I: Sequence[int], R: int, precision="fp32", split: int = 0):
+    """The recorded measured plan for this shape / rank / precision, or None."""
+    o = cpg_opts(_prec(precision), int(split), None, 0, None)
+    plan = cpg_gradient_plan()
+    if not lib().cpg_gradient_plan_query(_i64(I), len(I), int(R), ctypes.byref(o), ctypes.byref(plan)):
+        return None
+    return {"split": plan.split, "fused": bool(plan.fused)}
+
+
+def autotune_clear() -> None:
+    lib().cpg_autotune_clear()
 
 
 def cp_gradient_mode(Y, I: Sequence[int], A, n: int, Gn=None, *, precision="fp32", workspace=None, stream=None):

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -711,13 +712,90 @@ int choose_split(const Shape& s, const cpg_opts* opts) {
   return (opts && opts->split != 0) ? opts->split : split_point(s);
 }
 
+// ---- plan of the all-mode gradient: split k, one fused pass or two ----------------
+struct GradChoice {
+  int k = 1;
+  bool fused = false;
+};
+
+// Workspace bytes of the all-mode gradient under plan c.
+size_t grad_bytes(const Shape& s, int R, int prec, const GradChoice& c) {
+  LeadPlan pr = plan_lead(s, R, c.k, c.fused ? 3 : 1, prec);
+  if (!c.fused) pr.lpart_elems = std::max(pr.lpart_elems, plan_lead(s, R, c.k, 2, prec).lpart_elems);
+  size_t bytes = 0;
+  if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes);
+  else carve_grad<float>(nullptr, s, R, pr, &bytes);
+  return bytes;
+}
+
+// The planner's choice: n* (or the requested split) and the fused pass where
+// use_fused allows it.
+GradChoice default_choice(const Shape& s, int R, const cpg_opts* o) {
+  GradChoice c;
+  c.k = choose_split(s, o);
+  c.fused = use_fused(s, R, c.k, o ? o->precision : CPG_FP32);
+  return c;
+}
+
+// Plans the autotuner times: every split (or the requested one) x two passes,
+// and the fused pass where the precision has one and its partial sums stay
+// below the tensor's own size.
+std::vector<GradChoice> grad_candidates(const Shape& s, int R, const cpg_opts* o) {
+  std::vector<GradChoice> v;
+  const int prec = o->precision;
+  const int k0 = o->split != 0 ? o->split : 1, k1 = o->split != 0 ? o->split : s.N - 1;
+  for (int k = k0; k <= k1; ++k) {
+    GradChoice c;
+    c.k = k;
+    c.fused = false;
+    v.push_back(c);
+    if (prec != CPG_TF32X3) {
+      const LeadPlan f = plan_lead(s, R, k, 3, prec);
+      if (double(f.lpart_elems + f.rpart_elems) <= double(s.total)) {
+        c.fused = true;
+        v.push_back(c);
+      }
+    }
+  }
+  return v;
+}
+
+// Measured plans (cpg_autotune_gradient), per device, precision, requested
+// split, rank and shape.
+std::map<std::vector<int64_t>, GradChoice> g_tuned;
+std::mutex g_tuned_mu;
+
+std::vector<int64_t> tune_key(const Shape& s, int R, const cpg_opts* o) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int64_t> key = {dev, o ? o->precision : 0, o ? o->split : 0, R, s.N};
+  for (int n = 0; n < s.N; ++n) key.push_back(s.I[n]);
+  return key;
+}
+
+bool tuned_choice(const Shape& s, int R, const cpg_opts* o, GradChoice* c) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  auto it = g_tuned.find(tune_key(s, R, o));
+  if (it == g_tuned.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+// The plan cp_gradient_all runs: the measured one when there is one and the
+// workspace holds it, else the planner's.
+GradChoice grad_choice(const Shape& s, int R, const cpg_opts* o) {
+  GradChoice c;
+  if (tuned_choice(s, R, o, &c) && o->workspace_bytes >= grad_bytes(s, R, o->precision, c)) return c;
+  return default_choice(s, R, o);
+}
+
 // ---- all-mode gradient (Algorithm 2) ------------------------------------------------
 template <typename T>
 cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, int R, void* const* G,
-                             const cpg_opts* o) {
+                             const cpg_opts* o, const GradChoice& plan) {
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
-  const int k = choose_split(s, o);
-  const bool fused = use_fused(s, R, k, o->precision);
+  const int k = plan.k;
+  const bool fused = plan.fused;
   LeadPlan pr = plan_lead(s, R, k, fused ? 3 : 1, o->precision);
   LeadPlan pl = fused ? pr : plan_lead(s, R, k, 2, o->precision);
   // Workspace: one layout sized for the larger of the two plans.
@@ -1061,12 +1139,15 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
   if (opts && opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return 0;
   const int k = choose_split(s, opts);
   size_t bytes = 0;
+  cpg_opts od{};
+  if (opts) od = *opts;
+  od.precision = prec;
   if (call == CPG_CALL_GRADIENT_ALL) {
-    const bool fused = use_fused(s, R, k, prec);
-    LeadPlan pr = plan_lead(s, R, k, fused ? 3 : 1, prec);
-    if (!fused) pr.lpart_elems = std::max(pr.lpart_elems, plan_lead(s, R, k, 2, prec).lpart_elems);
-    if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes);
-    else carve_grad<float>(nullptr, s, R, pr, &bytes);
+    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od));
+    GradChoice t;
+    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t));
+  } else if (call == CPG_CALL_GRADIENT_TUNE) {
+    for (const GradChoice& c : grad_candidates(s, R, &od)) bytes = std::max(bytes, grad_bytes(s, R, prec, c));
   } else if (call == CPG_CALL_GRADIENT_MODE) {
     for (int n = 0; n < N; ++n) {
       size_t b = 0;
@@ -1092,8 +1173,83 @@ cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* c
   if (st != CPG_OK) return st;
   if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N))
     return CPG_ERR_ARG;
-  if (is_f64(opts->precision)) return gradient_all_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts);
-  return gradient_all_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts);
+  const GradChoice plan = grad_choice(s, R, opts);
+  if (is_f64(opts->precision)) return gradient_all_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts, plan);
+  return gradient_all_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts, plan);
+}
+
+cpg_status cpg_autotune_gradient(const void* Y, const int64_t* I, int N, const void* const* A, int R, void* const* G,
+                                 const cpg_opts* opts, int reps, cpg_gradient_plan* chosen) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N) || reps < 1 ||
+      reps > 1000)
+    return CPG_ERR_ARG;
+  const std::vector<GradChoice> cand = grad_candidates(s, R, opts);
+  size_t need = 0;
+  for (const GradChoice& c : cand) need = std::max(need, grad_bytes(s, R, opts->precision, c));
+  if (opts->workspace == nullptr || opts->workspace_bytes < need) return CPG_ERR_WORKSPACE;
+  cudaStream_t str = static_cast<cudaStream_t>(opts->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CPG_ERR_CUDA;
+  auto run = [&](const GradChoice& c) {
+    return is_f64(opts->precision)
+               ? gradient_all_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts, c)
+               : gradient_all_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts, c);
+  };
+  GradChoice best;
+  float best_ms = 0.f;
+  bool have = false;
+  for (const GradChoice& c : cand) {
+    st = run(c);  // first run: planning, attribute setup and warm caches outside the timing
+    if (st == CPG_OK && cudaEventRecord(e0, str) != cudaSuccess) st = CPG_ERR_CUDA;
+    for (int i = 0; i < reps && st == CPG_OK; ++i) st = run(c);
+    if (st == CPG_OK && (cudaEventRecord(e1, str) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      st = CPG_ERR_CUDA;
+    if (st != CPG_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= float(reps);
+    if (!have || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+      have = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != CPG_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_tuned[tune_key(s, R, opts)] = best;
+  }
+  if (chosen) {
+    chosen->split = best.k;
+    chosen->fused = best.fused ? 1 : 0;
+    chosen->ms = best_ms;
+    chosen->candidates = int(cand.size());
+  }
+  return CPG_OK;
+}
+
+int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_gradient_plan* plan) {
+  Shape s;
+  if (opts == nullptr || check_shape(I, N, R, s) != CPG_OK) return 0;
+  GradChoice c;
+  if (!tuned_choice(s, R, opts, &c)) return 0;
+  if (plan) {
+    plan->split = c.k;
+    plan->fused = c.fused ? 1 : 0;
+    plan->ms = 0.f;
+    plan->candidates = 0;
+  }
+  return 1;
+}
+
+void cpg_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  g_tuned.clear();
 }
 
 cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* const* A, int R, int n, void* Gn,

@@ -150,3 +150,26 @@ def test_status_strings(L):
     for s in range(8):
         assert cpgrad.status_str(s)
     assert cpgrad.status_str(99) == "unknown status"
+
+
+def test_autotune_arguments_and_sizes(L):
+    """The gradient autotuner checks its arguments before it launches
+    anything; its workspace covers every candidate plan."""
+    I = cpgrad._i64([4, 5, 6])
+    dummy = ctypes.c_void_p(16)
+    A = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    G = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    o = _opts()
+    plan = cpgrad.cpg_gradient_plan()
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cpg_autotune_gradient(None, I, 3, A, 3, G, ctypes.byref(o), 3, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_gradient(dummy, I, 3, A, 3, G, ctypes.byref(o), 0, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_gradient(dummy, I, 3, A, 3, G, None, 3, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_gradient(dummy, I, 3, A, 3, G, ctypes.byref(o), 3, None) == cpgrad.CPG_ERR_WORKSPACE
+    assert cpgrad.launch_count() == 0 * n0
+    for I_, R in (([100] * 4, 10), ([15] * 7, 20), ([30, 40, 50], 5)):
+        for prec in ("fp32", "bf16x3", "tf32x3"):
+            tune = cpgrad.cpg_workspace_size(I_, R, prec, 0, cpgrad.CALL_GRADIENT_TUNE)
+            assert tune >= cpgrad.cpg_workspace_size(I_, R, prec, 0, cpgrad.CALL_GRADIENT_ALL) > 0
+    cpgrad.autotune_clear()
+    assert cpgrad.gradient_plan([100] * 4, 10) is None
