@@ -12,10 +12,15 @@ Pins (all in ``tests/test_oracle.py``; none re-types the oracle's own code):
   * N = 2 reduces to the matrix products Y A2 and Y^T A1;
   * a hand-computed integer worked example (tests/golden/);
   * ALS: Eckart-Young on matrices (N = 2), fit -> 1 on noiseless low-rank
-    tensors, monotone cost, the cheap fit formula against the explicit one.
+    tensors, monotone cost, the cheap fit formula against the explicit one;
+  * the cost gradient of eq. 2.13 against central finite differences of
+    D (eq. 2.12), zero at an exact CP factorisation; a small first-order step
+    (eq. 2.15) lowers D;
+  * multiplicative NTF (eq. 2.18): an exact nonnegative factorisation is a
+    fixed point, D never rises, factors stay nonnegative.
 """
 from .cp_oracle import (  # noqa: F401
     unfold, khatri_rao, cp_gradient, cp_gradient_all, cp_gradient_entry,
     split_point, als_mode_order, gram_hadamard, cp_full, cp_fit_direct,
-    cp_als, AlsTrace,
+    cp_als, AlsTrace, cp_cost, cp_gradient_full, cp_gradient_step, cp_ntf, NtfTrace,
 )

@@ -202,3 +202,61 @@ def cp_als(y: np.ndarray, I: Sequence[int], A0: Sequence[np.ndarray], iters: int
         if direct_fit:
             fitsd.append(cp_fit_direct(yv, A, lam))
     return AlsTrace(A=A, lam=lam, fits=fits, fits_direct=fitsd)
+
+
+# ---- consumers of the gradient (Section 2.2) --------------------------------------
+def cp_cost(y: np.ndarray, A: Sequence[np.ndarray]) -> float:
+    """D = ||Y - Yhat||_F^2 (eq. 2.12), Yhat the CP model of the factors (no lambda)."""
+    y = np.asarray(y, dtype=np.float64)
+    r = y - cp_full(A)
+    return float(r @ r)
+
+
+def cp_gradient_full(y: np.ndarray, I: Sequence[int], A: Sequence[np.ndarray], n: int) -> np.ndarray:
+    """G^(n) of eq. 2.13 with the model term: E_(n) KR = Y_(n) KR - A^(n) Gamma^(n),
+    Gamma^(n) = Hadamard_{k != n} A^(k)T A^(k).  dD/dA^(n) = -2 G^(n)."""
+    return cp_gradient(y, I, A, n) - np.asarray(A[n], dtype=np.float64) @ gram_hadamard(A, skip=n)
+
+
+def cp_gradient_step(y: np.ndarray, I: Sequence[int], A: Sequence[np.ndarray], eta: float):
+    """One all-at-once first-order step (eq. 2.15): every gradient of eq. 2.13 at
+    the current factors, then a <- a + eta G for all modes at once (G is -1/2 the
+    derivative of D, so this is a <- a - (eta/2) dD/da).  Returns (new factors,
+    gradients)."""
+    A = [np.asarray(a, dtype=np.float64) for a in A]
+    G = [cp_gradient_full(y, I, A, n) for n in range(len(I))]
+    return [A[n] + eta * G[n] for n in range(len(I))], G
+
+
+@dataclasses.dataclass
+class NtfTrace:
+    A: list[np.ndarray]
+    fits: list[float]            # fit after each sweep (cheap formula)
+
+
+def cp_ntf(y: np.ndarray, I: Sequence[int], A0: Sequence[np.ndarray], iters: int,
+           order: Sequence[int] | None = None) -> NtfTrace:
+    """Multiplicative nonnegative CP updates (eq. 2.18) in the fast ALS mode
+    order of Section 4 (each mode uses the factors updated before it):
+        A^(n) <- A^(n) * (Y_(n) KR) / (A^(n) Gamma^(n)),
+    elementwise; an entry whose denominator is not positive is left as is.
+    No normalisation (the model is sum_r a_r^(1) o ... o a_r^(N)).  The fit after
+    a sweep uses the last mode's gradient as in cp_als, with lambda = 1."""
+    N = len(I)
+    A = [np.array(a, dtype=np.float64, copy=True) for a in A0]
+    if order is None:
+        order = als_mode_order(I)
+    yv = np.asarray(y, dtype=np.float64)
+    normY2 = float(yv @ yv)
+    fits = []
+    for _ in range(iters):
+        G = None
+        for n in order:
+            G = cp_gradient(yv, I, A, n)
+            D = A[n] @ gram_hadamard(A, skip=n)
+            A[n] = np.where(D > 0, A[n] * G / np.where(D > 0, D, 1.0), A[n])
+        last = order[-1]
+        inner = float(np.sum(A[last] * G))
+        model2 = float(np.sum(gram_hadamard(A, skip=None)))
+        fits.append(1.0 - np.sqrt(max(0.0, normY2 - 2.0 * inner + model2)) / np.sqrt(normY2))
+    return NtfTrace(A=A, fits=fits)

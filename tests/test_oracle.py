@@ -7,7 +7,12 @@ none of which re-types the oracle's own unfold-and-multiply code.
 * the invariant sum_i a_r^(n)[i] g_r^(n)[i] = Y x {a_r} for all n (eq. 2.6);
 * N = 2: G^(1) = Y A^(2), G^(2) = Y^T A^(1);
 * ALS (eq. 2.14): Eckart-Young on matrices, fit -> 1 on noiseless CP tensors,
-  monotone cost, cheap fit formula = explicit fit.
+  monotone cost, cheap fit formula = explicit fit;
+* the cost gradient of eq. 2.13 (both terms) against central differences of
+  D (eq. 2.12) summed entry by entry, and zero at an exact factorisation; a
+  small first-order step (eq. 2.15) lowers D by 2 eta ||G||^2 to first order;
+* multiplicative NTF (eq. 2.18): fixed point at an exact nonnegative
+  factorisation, non-increasing D, nonnegative factors, cheap fit = explicit.
 """
 import itertools
 import json
@@ -200,3 +205,97 @@ def test_cp_full_layout():
         want = sum(np.prod([A[m][idx[m], r] for m in range(3)]) for r in range(R))
         assert y[ivec(idx, I)] == pytest.approx(want, rel=1e-12, abs=1e-14)
     np.testing.assert_allclose(cpsynth.cp_model_vec(A), y, rtol=1e-12, atol=1e-14)
+
+
+# ---- consumers of the gradient: eq. 2.13 (model term), eq. 2.15, eq. 2.18 -------------
+def brute_cost(y, I, A):
+    """D = ||Y - Yhat||^2 (eq. 2.12) with Yhat entry by entry from eq. 2.7."""
+    R = A[0].shape[1]
+    D = 0.0
+    for idx in itertools.product(*[range(v) for v in I]):
+        yhat = sum(np.prod([A[m][idx[m], r] for m in range(len(I))]) for r in range(R))
+        D += (float(y[ivec(idx, I)]) - yhat) ** 2
+    return D
+
+
+@pytest.mark.parametrize("I,R", [([3, 4, 2], 2), ([2, 3, 2, 3], 3), ([4, 3], 2)])
+def test_full_gradient_is_minus_half_cost_derivative(I, R):
+    """Central differences of D (eq. 2.12, summed entry by entry) give
+    dD/dA^(n) = -2 G^(n) with G^(n) of eq. 2.13 (both terms)."""
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal(int(np.prod(I)))
+    A = [rng.standard_normal((In, R)) for In in I]
+    h = 1e-5
+    for n in range(len(I)):
+        G = oracle.cp_gradient_full(y, I, A, n)
+        for i in range(I[n]):
+            for r in range(R):
+                Ap = [a.copy() for a in A]
+                Am = [a.copy() for a in A]
+                Ap[n][i, r] += h
+                Am[n][i, r] -= h
+                fd = (brute_cost(y, I, Ap) - brute_cost(y, I, Am)) / (2 * h)
+                assert abs(fd - (-2.0 * G[i, r])) <= 1e-6 * max(1.0, abs(fd)), (n, i, r, fd, G[i, r])
+    assert abs(oracle.cp_cost(y, A) - brute_cost(y, I, A)) <= 1e-9 * brute_cost(y, I, A)
+
+
+@pytest.mark.parametrize("I,R", [([5, 6, 7], 3), ([4, 3, 5, 2], 2)])
+def test_full_gradient_vanishes_at_exact_factorisation(I, R):
+    A = cpsynth.gaussian_factors(I, R, seed=14)
+    y = cpsynth.cp_model_vec(A)
+    for n in range(len(I)):
+        G = oracle.cp_gradient_full(y, I, A, n)
+        scale = np.linalg.norm(oracle.cp_gradient(y, I, A, n))
+        assert np.linalg.norm(G) <= 1e-12 * scale
+
+
+def test_gradient_step_descends():
+    """eq. 2.15 along G (= -1/2 dD/da): D drops, to first order by 2 eta ||G||^2."""
+    I, R = [6, 5, 7], 3
+    p = cpsynth.make_problem(I, R, snr_db=10.0, seed=15, dtype=np.float64)
+    A = [a.copy() for a in p.init]
+    D0 = oracle.cp_cost(p.y, A)
+    eta = 1e-6
+    A1, G = oracle.cp_gradient_step(p.y, I, A, eta)
+    D1 = oracle.cp_cost(p.y, A1)
+    g2 = sum(float(np.sum(g * g)) for g in G)
+    assert D1 < D0
+    assert abs((D0 - D1) - 2 * eta * g2) <= 1e-3 * (2 * eta * g2)
+
+
+def _nonneg_problem(I, R, seed, noise):
+    rng = cpsynth.rng(seed, 7)
+    A = [np.abs(rng.standard_normal((In, R))) + 0.1 for In in I]
+    y = cpsynth.cp_model_vec(A)
+    y = y + noise * np.abs(rng.standard_normal(y.shape)) * np.std(y)
+    A0 = [np.abs(rng.standard_normal((In, R))) + 0.1 for In in I]
+    return y, A, A0
+
+
+def test_ntf_exact_factorisation_is_fixed_point():
+    """At an exact nonnegative factorisation Y_(n) KR = A^(n) Gamma^(n), so
+    eq. 2.18 multiplies every entry by one."""
+    I, R = [5, 4, 6], 2
+    y, A, _ = _nonneg_problem(I, R, 16, 0.0)
+    tr = oracle.cp_ntf(y, I, A, iters=2)
+    for n in range(len(I)):
+        assert np.allclose(tr.A[n], A[n], rtol=1e-12, atol=1e-14)
+    assert tr.fits[-1] > 1 - 1e-6
+
+
+def test_ntf_monotone_nonnegative_and_fit_formula():
+    """Multiplicative updates never raise D (Lee and Seung's auxiliary-function
+    argument applies mode by mode) and keep the factors nonnegative; the cheap
+    fit equals the explicit one."""
+    I, R = [7, 6, 5, 4], 3
+    y, _, A0 = _nonneg_problem(I, R, 17, 0.3)
+    A = [a.copy() for a in A0]
+    D = oracle.cp_cost(y, A)
+    for _ in range(6):
+        tr = oracle.cp_ntf(y, I, A, iters=1)
+        A = tr.A
+        Dn = oracle.cp_cost(y, A)
+        assert Dn <= D * (1 + 1e-12)
+        assert all(np.all(a >= 0) for a in A)
+        assert abs(tr.fits[-1] - oracle.cp_fit_direct(y, A, np.ones(R))) <= 1e-9
+        D = Dn
