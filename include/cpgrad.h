@@ -90,7 +90,9 @@ typedef enum {
   CPG_CALL_GRADIENT_ALL = 0,
   CPG_CALL_GRADIENT_MODE = 1,
   CPG_CALL_ALS = 2,
-  CPG_CALL_GRADIENT_TUNE = 3
+  CPG_CALL_GRADIENT_TUNE = 3,
+  CPG_CALL_GRADIENT_FULL = 4,  /* cp_gradient_full and cp_gradient_step */
+  CPG_CALL_NTF = 5             /* cp_ntf_iter */
 } cpg_call;
 
 /* n* = max{n : J_n <= K_n} of Algorithm 2 step 1, 1-based count of leading
@@ -165,6 +167,37 @@ cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* 
 cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
                        int iters, double* fit, const cpg_opts* opts);
 
+/* Cost gradient of eq. 2.13 for every mode, with its model term:
+ *     G[n] <- Y_(n) KR - A^(n) Gamma^(n),  Gamma^(n) = Hadamard_{m != n} A^(m)T A^(m),
+ * i.e. E_(n) KR for the residual E = Y - [[A]] without forming E.  The
+ * derivative of D = ||Y - Yhat||^2 (eq. 2.12) is -2 G[n].  Y_(n) KR comes from
+ * Algorithm 2 (the plan of cp_gradient_all, measured when tuned); Gamma^(n) and
+ * A^(n) Gamma^(n) are formed in FP64.  Workspace: cpg_workspace_size(...,
+ * CPG_CALL_GRADIENT_FULL).  Errors as for cp_gradient_all. */
+cpg_status cp_gradient_full(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                            void* const* G, const cpg_opts* opts);
+
+/* One all-at-once first-order step (eq. 2.15): G as cp_gradient_full at the
+ * current factors (every mode's gradient before any factor changes), then
+ * A[n] <- A[n] + eta G[n] for every n (a step of eta / 2 along -dD/da).
+ * A (device, in place) and G (device, out) as in cp_gradient_full; eta must
+ * not be NaN (CPG_ERR_ARG). */
+cpg_status cp_gradient_step(const void* Y, const int64_t* I, int N, void* const* A, int R, double eta,
+                            void* const* G, const cpg_opts* opts);
+
+/* `iters` sweeps of multiplicative nonnegative CP updates (eq. 2.18) in the
+ * fast CP_ALS order of Section 4 (modes k-1, ..., 0, then k, ..., N-1, the
+ * recursions using the factors just updated):
+ *     A^(n) <- A^(n) * (Y_(n) KR) / (A^(n) Gamma^(n))   elementwise,
+ * an entry whose denominator is not positive left as is; no normalisation.
+ * Meant for nonnegative Y and A (they then stay nonnegative).  fit (device,
+ * `iters` doubles, may be NULL) receives 1 - ||Y - Yhat|| / ||Y|| after each
+ * sweep, from R x R quantities.  The FP32 path forms Y_(n) KR in FP32 and the
+ * R x R products in FP64.  Workspace: cpg_workspace_size(..., CPG_CALL_NTF);
+ * R <= 64; argument errors as for cp_als_iter (no lambda). */
+cpg_status cp_ntf_iter(const void* Y, const int64_t* I, int N, void* const* A, int R, int iters, double* fit,
+                       const cpg_opts* opts);
+
 /* One member of a batched CP_ALS call.  Y, A[n], lambda and fit are device
  * buffers as in cp_als_iter; I and A are host arrays of N entries that are
  * read during the call only. */
@@ -233,7 +266,8 @@ int cpg_profile_lead(int enable);
 #define CPG_KIND_GRAM 12        /* Gram matrices                                */
 #define CPG_KIND_KRON 13        /* Kronecker vector of a run of modes           */
 #define CPG_KIND_NORM 14        /* ||Y||^2                                      */
-#define CPG_KIND_UPDATE 15      /* CP_ALS update, FP64 data                     */
+#define CPG_KIND_UPDATE 15      /* CP_ALS update (FP64 data), NTF update        */
+#define CPG_KIND_MODEL_TERM 16  /* model term of eq. 2.13, step of eq. 2.15     */
 
 /* Waits for and returns the recorded launch durations in milliseconds
  * (ms[i]) and each launch's kind (sides[i], CPG_KIND_*), at most `max`

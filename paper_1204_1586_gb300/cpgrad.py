@@ -22,11 +22,11 @@ LIB_PATH = os.path.join(_HERE, "libcpgrad.so")
 CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR_CUDA, CPG_ERR_TIMEOUT, \
     CPG_ERR_UNSUPPORTED = range(8)
 PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4}
-CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE = 0, 1, 2, 3
+CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE, CALL_GRADIENT_FULL, CALL_NTF = 0, 1, 2, 3, 4, 5
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
            "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read", "cpg_autotune_gradient",
-           "cpg_gradient_plan_query", "cpg_autotune_clear"]
+           "cpg_gradient_plan_query", "cpg_autotune_clear", "cp_gradient_full", "cp_gradient_step", "cp_ntf_iter"]
 
 
 class CpgError(RuntimeError):
@@ -101,6 +101,15 @@ def lib() -> ctypes.CDLL:
         L.cpg_gradient_plan_query.restype = ctypes.c_int
         L.cpg_autotune_clear.argtypes = []
         L.cpg_autotune_clear.restype = None
+        L.cp_gradient_full.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, vpp,
+                                       ctypes.POINTER(cpg_opts)]
+        L.cp_gradient_full.restype = ctypes.c_int
+        L.cp_gradient_step.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, ctypes.c_double, vpp,
+                                       ctypes.POINTER(cpg_opts)]
+        L.cp_gradient_step.restype = ctypes.c_int
+        L.cp_ntf_iter.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.POINTER(cpg_opts)]
+        L.cp_ntf_iter.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -136,7 +145,8 @@ def launch_count(reset: bool = False) -> int:
 
 # Launch kinds of the timing record (cpgrad.h CPG_KIND_*).
 LAUNCH_KINDS = {1: "lead_step4_R", 2: "lead_step7_L", 3: "lead_step4+7_fused", 10: "chain_segmented_dot",
-                11: "als_mode_fused_update", 12: "gram", 13: "kronecker_vector", 14: "norm_y2", 15: "als_update_fp64"}
+                11: "als_mode_fused_update", 12: "gram", 13: "kronecker_vector", 14: "norm_y2",
+                15: "als_update_fp64_or_ntf", 16: "gradient_model_term"}
 
 
 def profile_lead(enable) -> None:
@@ -282,6 +292,65 @@ def cp_gradient_autotune(Y, I: Sequence[int], A, G=None, *, precision="fp32", sp
     if st != CPG_OK:
         raise CpgError(st, "cpg_autotune_gradient")
     return {"split": plan.split, "fused": bool(plan.fused), "ms": float(plan.ms), "candidates": plan.candidates}
+
+
+def _grad_args(Y, I, A, G, precision):
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for n, a in enumerate(A):
+        _check_colmajor(a, int(I[n]), R, dtype, f"A[{n}]")
+    if G is None:
+        G = [torch.empty((R, int(In)), dtype=dtype, device=Y.device).t() for In in I]
+    for n, g in enumerate(G):
+        _check_colmajor(g, int(I[n]), R, dtype, f"G[{n}]")
+    return R, G
+
+
+def cp_gradient_full(Y, I: Sequence[int], A, G=None, *, precision="fp32", split: int = 0, workspace=None,
+                     stream=None):
+    """Cost gradient of eq. 2.13 with its model term, Y_(n) KR - A^(n) Gamma^(n), every mode."""
+    R, G = _grad_args(Y, I, A, G, precision)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_GRADIENT_FULL), _stream_ptr(stream))
+    st = lib().cp_gradient_full(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, _ptrs(G), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_gradient_full")
+    return G
+
+
+def cp_gradient_step(Y, I: Sequence[int], A, eta: float, G=None, *, precision="fp32", split: int = 0,
+                     workspace=None, stream=None):
+    """One all-at-once first-order step (eq. 2.15): G = cost gradients at A, then A += eta G (in place)."""
+    R, G = _grad_args(Y, I, A, G, precision)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_GRADIENT_FULL), _stream_ptr(stream))
+    st = lib().cp_gradient_step(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, float(eta), _ptrs(G),
+                                ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_gradient_step")
+    return G
+
+
+def cp_ntf_iter(Y, I: Sequence[int], A, iters: int, fit=None, *, precision="fp32", split: int = 0, workspace=None,
+                stream=None):
+    """`iters` multiplicative nonnegative CP sweeps (eq. 2.18), A updated in place; returns the fits."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for n, a in enumerate(A):
+        _check_colmajor(a, int(I[n]), R, dtype, f"A[{n}]")
+    if fit is None:
+        fit = torch.zeros(max(int(iters), 1), dtype=torch.float64, device=Y.device)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_NTF), _stream_ptr(stream))
+    st = lib().cp_ntf_iter(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A), R, int(iters),
+                           ctypes.c_void_p(fit.data_ptr()), ctypes.byref(o))
+    if st != CPG_OK:
+        raise CpgError(st, "cp_ntf_iter")
+    return fit
 
 
 def gradient_plan(I: Sequence[int], R: int, precision="fp32", split: int = 0):

@@ -13,6 +13,7 @@
 #include "als_df.cuh"
 #include "chain.cuh"
 #include "common.cuh"
+#include "consumers.cuh"
 #include "lead_dispatch.cuh"
 #include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
@@ -44,7 +45,8 @@ enum LaunchKind : int {
   kKindGram = 12,    // Gram matrices of all factors
   kKindKron = 13,    // Kronecker vector of a run of modes
   kKindNorm = 14,    // ||Y||^2 from partial sums
-  kKindUpdate = 15   // ALS update (FP64 data)
+  kKindUpdate = 15,  // ALS update (FP64 data), multiplicative update (eq. 2.18)
+  kKindModelTerm = 16  // model term of the cost gradient (eq. 2.13) and first-order step (eq. 2.15)
 };
 
 // Records a start event at construction and an end event at destruction when
@@ -860,6 +862,59 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   return cuda_status(cudaGetLastError());
 }
 
+// ---- cost gradient of eq. 2.13, first-order step of eq. 2.15 -------------------------
+// Workspace: the all-mode gradient's, then the FP64 Grams and Gamma^(n) in its
+// last grams_bytes (at a 256-byte boundary).
+inline size_t grams_bytes(int N, int R) { return 2 * align_up(size_t(N) * R * R * sizeof(double)); }
+
+template <typename T>
+cpg_status gradient_full_impl(const Shape& s, const T* Y, void* const* A, int R, void* const* G, const cpg_opts* o,
+                              double eta, bool step) {
+  const size_t gb = grams_bytes(s.N, R);
+  if (o->workspace == nullptr || o->workspace_bytes < gb + kAlign) return CPG_ERR_WORKSPACE;
+  cpg_opts og = *o;
+  og.workspace_bytes = (o->workspace_bytes - gb) / kAlign * kAlign;
+  double* grams = reinterpret_cast<double*>(static_cast<char*>(o->workspace) + og.workspace_bytes);
+  double* gammas = reinterpret_cast<double*>(reinterpret_cast<char*>(grams) + gb / 2);
+  // Y_(n) KR for every mode (Algorithm 2) at the current factors.
+  const void* const* Ac = const_cast<const void* const*>(A);
+  cpg_status st = gradient_all_impl<T>(s, Y, Ac, R, G, &og, grad_choice(s, R, &og));
+  if (st != CPG_OK) return st;
+  cudaStream_t str = static_cast<cudaStream_t>(o->stream);
+  ++g_launches;
+  {
+    Timed timer(str, kKindGram);
+    launch_pdl(gram_all_kernel<T>, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, str, fac_args<T>(s, Ac),
+               R, grams);
+  }
+  ++g_launches;
+  {
+    Timed timer(str, kKindGram);
+    launch_pdl(gamma_all_kernel, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, str,
+               static_cast<const double*>(grams), s.N, R, gammas);
+  }
+  ModelTermArgs<T> a{};
+  a.N = s.N;
+  a.R = R;
+  int64_t imax = 1;
+  for (int n = 0; n < s.N; ++n) {
+    a.I[n] = s.I[n];
+    a.A[n] = static_cast<T*>(A[n]);
+    a.G[n] = static_cast<T*>(G[n]);
+    imax = std::max(imax, s.I[n]);
+  }
+  a.gammas = gammas;
+  a.eta = eta;
+  a.step = step ? 1 : 0;
+  ++g_launches;
+  {
+    Timed timer(str, kKindModelTerm);
+    launch_pdl(model_term_kernel<T>, dim3(blocks_for(imax, kRowsPerBlock, 1 << 30), s.N), dim3(256),
+               size_t(kRowsPerBlock) * R * sizeof(double), str, a);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 // ---- single-mode gradient (Section 3.2) ----------------------------------------------
 template <typename T>
 cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, int R, int n, T* Gn,
@@ -889,9 +944,12 @@ cpg_status gradient_mode_impl(const Shape& s, const T* Y, const void* const* A, 
 // ---- fast CP_ALS (Section 4) -------------------------------------------------------
 constexpr int kAlsMaxRank = 64;
 
+// mu = false: fast CP_ALS (eq. 2.14); mu = true: the same sweep with the
+// multiplicative nonnegative update of eq. 2.18 in place of the solve (no
+// normalisation, lambda unused).
 template <typename T>
 cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, int R, int iters, double* fit,
-                    const cpg_opts* o, int* status_override = nullptr) {
+                    const cpg_opts* o, int* status_override = nullptr, bool mu = false) {
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
   if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
   const int k = choose_split(s, o);
@@ -906,31 +964,38 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   const void* const* Ac = const_cast<const void* const*>(A);
 
   constexpr bool kDf = std::is_same_v<T, float>;
+  const bool fused = kDf && !mu;  // FP32 least squares: the fused mode kernels
   int64_t imax = 1;
   for (int m = 0; m < s.N; ++m) imax = std::max(imax, s.I[m]);
   constexpr size_t kSmemCap = 200 * 1024;
   const bool smem_path = (kDf ? als_df_smem_bytes(imax, R) : als_smem_bytes(imax, R)) <= kSmemCap;
-  if (kDf && !smem_path) return CPG_ERR_UNSUPPORTED;
+  if (fused && !smem_path) return CPG_ERR_UNSUPPORTED;
   const size_t upd_smem = size_t(3) * R * R * sizeof(double);
   if constexpr (!kDf) {
     cudaFuncSetAttribute(als_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(upd_smem));
     if (smem_path)
       cudaFuncSetAttribute(als_update_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(als_smem_bytes(imax, R)));
-  } else {
+  } else if (fused) {
     // The fused mode kernels' CTA ticket starts at zero.
     if (cudaMemsetAsync(w.h.ticket, 0, sizeof(unsigned int), st) != cudaSuccess) return CPG_ERR_CUDA;
   }
 
   ++g_launches;
-  if constexpr (kDf) {
+  {
+    // Double-float Grams for the fused FP32 path, FP64 otherwise.
     Timed timer(st, kKindGram);
-    launch_pdl(gram_all_df_kernel, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac), R,
-               reinterpret_cast<df*>(w.grams));
-  } else {
-    Timed timer(st, kKindGram);
-    launch_pdl(gram_all_kernel<T>, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac), R,
-               w.grams);
+    bool done = false;
+    if constexpr (kDf) {
+      if (fused) {
+        launch_pdl(gram_all_df_kernel, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac),
+                   R, reinterpret_cast<df*>(w.grams));
+        done = true;
+      }
+    }
+    if (!done)
+      launch_pdl(gram_all_kernel<T>, dim3(blocks_for(int64_t(R) * R, 256), s.N), dim3(256), 0, st, fac_args<T>(s, Ac),
+                 R, w.grams);
   }
 
   // The update of mode n from G^(n) = Gn.  FP32 data: fused into the kernel
@@ -938,26 +1003,55 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   // after the G kernel.
   auto update = [&](int n, const SegDot<T>& sd, double* fit_out) {
     if constexpr (kDf) {
-      AlsDfArgs u{};
+      if (!mu) {
+        AlsDfArgs u{};
+        u.N = s.N;
+        u.n = n;
+        u.R = R;
+        u.In = s.I[n];
+        u.grams = reinterpret_cast<df*>(w.grams);
+        u.V = reinterpret_cast<df*>(w.V);
+        u.Vi = reinterpret_cast<df*>(w.Vi);
+        u.G = sd.out;
+        u.An = static_cast<float*>(A[n]);
+        u.lambda = lambda;
+        u.status = w.h.status;
+        u.fit_out = fit_out;
+        u.normY2 = w.h.normY2;
+        launch_mode_update(sd, u, w.h.ticket, st);
+        return;
+      }
+    }
+    const bool identity = sd.inner == 1 && sd.nparts == 1 && sd.X == sd.out;
+    if (!identity) launch_seg(sd, st);
+    ++g_launches;
+    Timed timer(st, kKindUpdate);
+    if (mu) {
+      // eq. 2.18, then the Gram of the new factor (and the fit after the last mode).
+      MuArgs<T> u{};
       u.N = s.N;
       u.n = n;
       u.R = R;
       u.In = s.I[n];
-      u.grams = reinterpret_cast<df*>(w.grams);
-      u.V = reinterpret_cast<df*>(w.V);
-      u.Vi = reinterpret_cast<df*>(w.Vi);
+      u.grams = w.grams;
       u.G = sd.out;
-      u.An = static_cast<float*>(A[n]);
-      u.lambda = lambda;
-      u.status = w.h.status;
-      u.fit_out = fit_out;
-      u.normY2 = w.h.normY2;
-      launch_mode_update(sd, u, w.h.ticket, st);
-    } else {
-      const bool identity = sd.inner == 1 && sd.nparts == 1 && sd.X == sd.out;
-      if (!identity) launch_seg(sd, st);
+      u.An = static_cast<T*>(A[n]);
+      const size_t sm = size_t(R + kRowsPerBlock) * R * sizeof(double);
+      launch_pdl(mu_update_kernel<T>, dim3(blocks_for(s.I[n], kRowsPerBlock, 1 << 30)), dim3(256), sm, st, u);
+      FacArgs<T> f{};
+      f.I[0] = s.I[n];
+      f.A[0] = static_cast<const T*>(A[n]);
       ++g_launches;
-      Timed timer(st, kKindUpdate);
+      launch_pdl(gram_all_kernel<T>, dim3(blocks_for(int64_t(R) * R, 256), 1), dim3(256), 0, st, f, R,
+                 w.grams + int64_t(n) * R * R);
+      if (fit_out != nullptr) {
+        ++g_launches;
+        launch_pdl(ntf_fit_kernel<T>, dim3(1), dim3(256), 0, st, s.N, R, s.I[n], static_cast<const T*>(A[n]), sd.out,
+                   static_cast<const double*>(w.grams), static_cast<const double*>(w.h.normY2), fit_out);
+      }
+      return;
+    }
+    if constexpr (!kDf) {
       AlsArgs<T> u{};
       u.N = s.N;
       u.n = n;
@@ -978,8 +1072,8 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     }
   };
   // G^(n) of a mode whose finishing contraction is the identity (a single
-  // remaining mode with no partial sums): X itself.  FP64 data reads it in
-  // place; FP32 data copies it into w.G inside the fused kernel.
+  // remaining mode with no partial sums): X itself.  The fused FP32 path
+  // copies it into w.G inside its mode kernel; the others read it in place.
   auto identity_seg = [&](const T* X, int64_t In) {
     SegDot<T> p{};
     p.X = X;
@@ -989,7 +1083,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     p.astep = 1;
     p.ustep = 1;
     p.inner = 1;
-    p.out = kDf ? w.G : const_cast<T*>(X);
+    p.out = fused ? w.G : const_cast<T*>(X);
     p.R = R;
     return p;
   };
@@ -1028,7 +1122,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
           // Recursion with the updated a^(m) (eq. 3.20).  When the next mode is
           // mode 0, the contracted tensor is G^(0) itself: its update is fused.
           const T* src = Xred ? Xred : X;
-          if (kDf && m == 1) {
+          if (fused && m == 1) {
             update(0, contract_seg<T, true>(src, len_o, In, R, static_cast<const T*>(A[m]), w.G), nullptr);
             g_done = true;
           } else {
@@ -1068,7 +1162,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
           // Recursion with the updated a^(n) (eq. 3.22); fused with the update
           // of mode N-1 when that is the next mode.
           const T* src = Xred ? Xred : X;
-          if (kDf && n + 1 == s.N - 1) {
+          if (fused && n + 1 == s.N - 1) {
             update(n + 1, contract_seg<T, false>(src, len_o, In, R, static_cast<const T*>(A[n]), w.G), fit_of(n + 1));
             g_done = true;
           } else {
@@ -1146,6 +1240,11 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
     bytes = grad_bytes(s, R, prec, default_choice(s, R, &od));
     GradChoice t;
     if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t));
+  } else if (call == CPG_CALL_GRADIENT_FULL) {
+    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od));
+    GradChoice t;
+    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t));
+    bytes = align_up(bytes) + grams_bytes(N, R) + kAlign;
   } else if (call == CPG_CALL_GRADIENT_TUNE) {
     for (const GradChoice& c : grad_candidates(s, R, &od)) bytes = std::max(bytes, grad_bytes(s, R, prec, c));
   } else if (call == CPG_CALL_GRADIENT_MODE) {
@@ -1156,7 +1255,7 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
       else carve_mode<float>(nullptr, s, R, n, rt, &b);
       bytes = std::max(bytes, b);
     }
-  } else if (call == CPG_CALL_ALS) {
+  } else if (call == CPG_CALL_ALS || call == CPG_CALL_NTF) {
     const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
     if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes);
     else carve_als<float>(nullptr, s, R, lr, ll, &bytes);
@@ -1273,6 +1372,44 @@ cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, d
   if (iters == 0) return CPG_OK;
   if (is_f64(opts->precision)) return als_impl<double>(s, static_cast<const double*>(Y), A, lambda, R, iters, fit, opts);
   return als_impl<float>(s, static_cast<const float*>(Y), A, lambda, R, iters, fit, opts);
+}
+
+cpg_status cp_gradient_full(const void* Y, const int64_t* I, int N, const void* const* A, int R, void* const* G,
+                            const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N))
+    return CPG_ERR_ARG;
+  void* const* Am = const_cast<void* const*>(A);  // read only: no step
+  if (is_f64(opts->precision))
+    return gradient_full_impl<double>(s, static_cast<const double*>(Y), Am, R, G, opts, 0.0, false);
+  return gradient_full_impl<float>(s, static_cast<const float*>(Y), Am, R, G, opts, 0.0, false);
+}
+
+cpg_status cp_gradient_step(const void* Y, const int64_t* I, int N, void* const* A, int R, double eta, void* const* G,
+                            const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || G == nullptr ||
+      !ptrs_ok(const_cast<const void* const*>(G), N) || !(eta == eta))
+    return CPG_ERR_ARG;
+  if (is_f64(opts->precision))
+    return gradient_full_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts, eta, true);
+  return gradient_full_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts, eta, true);
+}
+
+cpg_status cp_ntf_iter(const void* Y, const int64_t* I, int N, void* const* A, int R, int iters, double* fit,
+                       const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || iters < 0) return CPG_ERR_ARG;
+  if (iters == 0) return CPG_OK;
+  if (is_f64(opts->precision))
+    return als_impl<double>(s, static_cast<const double*>(Y), A, nullptr, R, iters, fit, opts, nullptr, true);
+  return als_impl<float>(s, static_cast<const float*>(Y), A, nullptr, R, iters, fit, opts, nullptr, true);
 }
 
 cpg_status cpg_workspace_init(const cpg_opts* opts) {

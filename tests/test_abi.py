@@ -173,3 +173,28 @@ def test_autotune_arguments_and_sizes(L):
             assert tune >= cpgrad.cpg_workspace_size(I_, R, prec, 0, cpgrad.CALL_GRADIENT_ALL) > 0
     cpgrad.autotune_clear()
     assert cpgrad.gradient_plan([100] * 4, 10) is None
+
+
+def test_consumer_entry_points_check_arguments(L):
+    """cp_gradient_full / cp_gradient_step / cp_ntf_iter return argument and
+    workspace errors before launching anything."""
+    I = cpgrad._i64([4, 5, 6])
+    dummy = ctypes.c_void_p(16)
+    A = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    G = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    o = _opts()
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cp_gradient_full(None, I, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_gradient_full(dummy, I, 3, A, 3, None, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_gradient_full(dummy, I, 3, A, 3, G, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_gradient_step(dummy, I, 3, A, 3, float("nan"), G, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_gradient_step(dummy, I, 3, A, 3, 0.1, G, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_ntf_iter(dummy, I, 3, A, 3, -1, None, ctypes.byref(o)) == cpgrad.CPG_ERR_ARG
+    assert L.cp_ntf_iter(dummy, I, 3, A, 3, 0, None, ctypes.byref(o)) == cpgrad.CPG_OK    # nothing to do
+    assert L.cp_ntf_iter(dummy, I, 3, A, 3, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_WORKSPACE
+    assert L.cp_ntf_iter(dummy, I, 3, A, 65, 2, None, ctypes.byref(o)) == cpgrad.CPG_ERR_UNSUPPORTED
+    assert cpgrad.launch_count() == 0 * n0
+    full = cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_FULL)
+    assert full > cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
+    assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_NTF) == \
+        cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_ALS)
