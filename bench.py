@@ -432,6 +432,19 @@ def main():
     line["gradient_frac_of_one_pass_roofline"] = (ybytes / hbm / 1e6) / tg
     line["als_iter_per_s"] = 1e3 / ta
     line["als_frac_of_two_pass_roofline"] = (2 * ybytes / hbm / 1e6) / ta
+    # The gradient's consumers on the same tensor (informational): the cost
+    # gradient of eq. 2.13, one first-order step (eq. 2.15), and multiplicative
+    # NTF sweeps (eq. 2.18) on |Y| with nonnegative factors.
+    line["cost_gradient_ms"] = _time_component(
+        lambda: cg.cp_gradient_full(Y, I, A0, G, workspace=ws, precision=prec), stream)
+    Ast = [a.clone() for a in A0]
+    line["gradient_step_ms"] = _time_component(
+        lambda: cg.cp_gradient_step(Y, I, Ast, 1e-9, G, workspace=ws, precision=prec), stream)
+    Yabs = Y.abs()
+    Ann = [cg.colmajor(a.abs()) for a in A0]
+    line["ntf_sweep_ms"] = _time_component(
+        lambda: cg.cp_ntf_iter(Yabs, I, [a.clone() for a in Ann], 5, workspace=ws, precision=prec), stream) / 5
+    del Yabs
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
