@@ -241,6 +241,16 @@ cpg_status cpg_workspace_init(const cpg_opts* opts);
  * last call (CPG_OK if none) and clears it. */
 cpg_status cpg_device_status(const cpg_opts* opts);
 
+/* Failure-detection self-test (the paper has no counterpart).  Launches, on
+ * opts->stream, one CTA whose mbarrier wait can never complete (nothing
+ * arrives on the barrier), bounded by `polls` polls (1 .. 2^24) exactly as
+ * every wait in this library's kernels is.  On expiry the CTA records
+ * CPG_ERR_TIMEOUT in the status word at the start of opts->workspace and
+ * returns: no fault, no hang, the context stays usable, and
+ * cpg_device_status() reports the timeout.  CPG_ERR_ARG for a NULL workspace,
+ * one smaller than 256 bytes, or polls out of range. */
+cpg_status cpg_selftest_timeout(const cpg_opts* opts, unsigned polls);
+
 /* Static description of a status code. */
 const char* cpg_status_str(int status);
 

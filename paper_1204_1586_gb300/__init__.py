@@ -6,6 +6,6 @@ of ``include/cpgrad.h``; ``cpgrad`` is its argument-marshalling binding.
 from .cpgrad import (  # noqa: F401
     cpg_split_point, cpg_workspace_size, cp_gradient_all, cp_gradient_mode, cp_als_iter, cp_als_batched,
     cpg_device_status, cp_gradient_autotune, gradient_plan, autotune_clear, cp_gradient_full, cp_gradient_step,
-    cp_ntf_iter,
+    cp_ntf_iter, selftest_timeout,
     colmajor, launch_count, profile_lead, profile_read, Workspace, CpgError, PRECISIONS, LAUNCH_KINDS, lib,
 )

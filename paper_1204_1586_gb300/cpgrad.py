@@ -26,7 +26,8 @@ CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE, CALL_GRADIE
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
            "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read", "cpg_autotune_gradient",
-           "cpg_gradient_plan_query", "cpg_autotune_clear", "cp_gradient_full", "cp_gradient_step", "cp_ntf_iter"]
+           "cpg_gradient_plan_query", "cpg_autotune_clear", "cp_gradient_full", "cp_gradient_step", "cp_ntf_iter",
+           "cpg_selftest_timeout"]
 
 
 class CpgError(RuntimeError):
@@ -110,6 +111,8 @@ def lib() -> ctypes.CDLL:
         L.cp_ntf_iter.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.POINTER(cpg_opts)]
         L.cp_ntf_iter.restype = ctypes.c_int
+        L.cpg_selftest_timeout.argtypes = [ctypes.POINTER(cpg_opts), ctypes.c_uint]
+        L.cpg_selftest_timeout.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -446,6 +449,17 @@ def cp_als_batched(members, iters: int, *, precision="fp32", split: int = 0, wor
     if st != CPG_OK:
         raise CpgError(st, "cp_als_batched")
     return out
+
+
+def selftest_timeout(polls: int = 4096, workspace=None, device=None, stream=None) -> None:
+    """Launch the bounded-wait self-test: a wait that can never complete gives up
+    after `polls` polls and records CPG_ERR_TIMEOUT in the workspace's status word
+    (read it with cpg_device_status)."""
+    ws = _ws_for(workspace, device)
+    o = _opts(0, 0, ws, 256, _stream_ptr(stream))
+    st = lib().cpg_selftest_timeout(ctypes.byref(o), int(polls))
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_selftest_timeout")
 
 
 def cpg_device_status(workspace=None, device=None, stream=None) -> int:

@@ -1179,6 +1179,20 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   return cuda_status(cudaGetLastError());
 }
 
+// ---- failure detection ----------------------------------------------------------------
+// One CTA waits on an mbarrier phase that nothing completes, with the bounded
+// wait every kernel of this library uses; on expiry it records
+// CPG_ERR_TIMEOUT in the status word and returns.
+__global__ void timeout_selftest_kernel(int* status, uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0u, polls)) atomicCAS(status, 0, int(CPG_ERR_TIMEOUT));
+}
+
 // ---- batched CP_ALS ------------------------------------------------------------------
 struct StreamPool {
   cudaStream_t s[kPoolStreams] = {};
@@ -1410,6 +1424,16 @@ cpg_status cp_ntf_iter(const void* Y, const int64_t* I, int N, void* const* A, i
   if (is_f64(opts->precision))
     return als_impl<double>(s, static_cast<const double*>(Y), A, nullptr, R, iters, fit, opts, nullptr, true);
   return als_impl<float>(s, static_cast<const float*>(Y), A, nullptr, R, iters, fit, opts, nullptr, true);
+}
+
+cpg_status cpg_selftest_timeout(const cpg_opts* opts, unsigned polls) {
+  if (opts == nullptr || opts->workspace == nullptr || opts->workspace_bytes < kAlign || polls < 1 ||
+      polls > (1u << 24))
+    return CPG_ERR_ARG;
+  ++g_launches;
+  timeout_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(opts->stream)>>>(static_cast<int*>(opts->workspace),
+                                                                                 polls);
+  return cuda_status(cudaGetLastError());
 }
 
 cpg_status cpg_workspace_init(const cpg_opts* opts) {

@@ -198,3 +198,14 @@ def test_consumer_entry_points_check_arguments(L):
     assert full > cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
     assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_NTF) == \
         cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_ALS)
+
+
+def test_selftest_timeout_arguments(L):
+    dummy = ctypes.c_void_p(256)
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cpg_selftest_timeout(None, 16) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_selftest_timeout(ctypes.byref(_opts()), 16) == cpgrad.CPG_ERR_ARG            # no workspace
+    assert L.cpg_selftest_timeout(ctypes.byref(_opts(ws=dummy, nbytes=64)), 16) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_selftest_timeout(ctypes.byref(_opts(ws=dummy, nbytes=256)), 0) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_selftest_timeout(ctypes.byref(_opts(ws=dummy, nbytes=256)), (1 << 24) + 1) == cpgrad.CPG_ERR_ARG
+    assert cpgrad.launch_count() == 0 * n0
