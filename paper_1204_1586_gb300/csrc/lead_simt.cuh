@@ -233,16 +233,21 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   // Element copies commit one cp.async group per call, empty past the last
   // stage, so that "all but STAGES - 2 groups complete" always means "stage
   // it has landed".
-  int issued = 0;  // stages issued so far
-  auto issue = [&](int it) {
+  int issued = 0;               // stages issued so far
+  int iss_ci = 0, iss_rt = 0;   // column chunk and row tile of stage `issued`
+  auto issue = [&](int it) {    // it == issued, or past the last stage
     if (it >= nst) {
       if (!use_tma) cp_async_commit();
       return;
     }
     issued = it + 1;
     T* dst = Ys + size_t(it % STAGES) * TK * TJ;
-    const int64_t cbase = kbeg + int64_t(it / nrt) * TK;
-    const int64_t j0 = jblk + int64_t(it % nrt) * TJ;
+    const int64_t cbase = kbeg + int64_t(iss_ci) * TK;
+    const int64_t j0 = jblk + int64_t(iss_rt) * TJ;
+    if (++iss_rt == nrt) {
+      iss_rt = 0;
+      ++iss_ci;
+    }
     if (use_tma) {
       if (tid == 0) {
         tc::fence_async_smem();
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   };
   auto fetch_wr = [&](int it2) {
     if (it2 < nst)
-      fetch_rows(a.wr, kbeg + int64_t(it2 / nrt) * TK + cw, K, rw, C::RSTEP,
+      fetch_rows(a.wr, kbeg + int64_t(it2) * TK + cw, K, rw, C::RSTEP,  // R side: one row tile per J-block
                  std::integral_constant<int, C::EWR>{}, pwa, pwq);
   };
   auto store_wr = [&](int it2) {
@@ -310,10 +315,9 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       if (r < RT) Wr[cw * RT + r] = pwa[u] * pwq[u];
     }
   };
-  auto fetch_wl = [&](int it2) {
-    if (it2 < nst)
-      fetch_rows(a.wl, jblk + int64_t(it2 % nrt) * TJ + jw, J, rl, C::LSTEP,
-                 std::integral_constant<int, C::EWL>{}, pla, plq);
+  // W_L rows of row tile t of this J-block.
+  auto fetch_wl = [&](int t) {
+    fetch_rows(a.wl, jblk + int64_t(t) * TJ + jw, J, rl, C::LSTEP, std::integral_constant<int, C::EWL>{}, pla, plq);
   };
   auto store_wl = [&](T* Wl) {
 #pragma unroll
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     // Khatri-Rao rows of the next stage: loads now, products stored after this
     // stage's arithmetic (into the buffer the previous stage used).
     if constexpr (DO_R) fetch_wr(it + 1);
-    if (wl_per_stage) fetch_wl(it + 1);
+    if (wl_per_stage && it + 1 < nst) fetch_wl(rt + 1 == nrt ? 0 : rt + 1);
 
     T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
     if constexpr (DO_R) {
