@@ -19,9 +19,11 @@
 // recorded in the device status word.
 // Every quantity of the normal equations is a double-float (about 48-bit
 // significand) so that their conditioning is handled at FP64-like accuracy on
-// the FP32 pipe; the measured FP64 rate of this GPU (64-cycle dependent FMA,
-// ~680-cycle divide) would put tens of microseconds on the critical path of
-// every update.
+// the FP32 pipe; the sums of products G V^{-1}, ||x_q||^2 and Gram_n are
+// accumulated by the compensated dot product of dfloat.cuh, as accurate at
+// about half the instructions and a far shorter dependent chain.  The
+// measured FP64 rate of this GPU (64-cycle dependent FMA, ~680-cycle divide)
+// would put tens of microseconds on the critical path of every update.
 //
 // The update runs inside the kernel that produces G (als_mode_df_kernel):
 // every CTA but one computes its share of G (a finishing contraction or a
@@ -149,9 +151,9 @@ __device__ __forceinline__ df df_warp_sum(df v) {
 
 // Phases (each a short dependent chain, all entries in parallel):
 //   load     V^{-1}, V (from the inverse CTA), G;
-//   X        = G V^{-1}, one output per thread;
-//   lambda   warp per column; a_q = x_q / lambda_q;
-//   Gram_n   8 lanes per (p, q) pair;
+//   X        = G V^{-1}, one output per thread (compensated dot product);
+//   lambda   warp per column (compensated sum of squares); a_q = x_q / lambda_q;
+//   Gram_n   8 lanes per (p, q) pair (compensated dot products);
 //   fit      <Y, Yhat> = sum_q lambda_q <a_q, g_q>,
 //            ||Yhat||^2 = lambda^T (V * Gram_n) lambda.
 __device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
@@ -175,39 +177,44 @@ __device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
     Vis[t] = df{vi.x, vi.y};
     Vs[t] = df{v.x, v.y};
   }
-  for (int t = tid; t < In * R; t += nt) {
-    const int q = t / In, i = t - q * In;
-    Gs[i * RS + q] = __ldcg(a.G + t);
+  // Every load of a round in flight before its stores.
+  constexpr int kLoadUnroll = 4;
+  for (int t0 = tid; t0 < In * R; t0 += kLoadUnroll * nt) {
+    float v[kLoadUnroll];
+#pragma unroll
+    for (int k = 0; k < kLoadUnroll; ++k) {
+      const int t = t0 + k * nt;
+      v[k] = (t < In * R) ? __ldcg(a.G + t) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kLoadUnroll; ++k) {
+      const int t = t0 + k * nt;
+      if (t < In * R) {
+        const int q = t / In, i = t - q * In;
+        Gs[i * RS + q] = v[k];
+      }
+    }
   }
   __syncthreads();
   if (!(Vis[0].hi != 0.f)) return;  // V was not positive definite: leave this mode untouched
 
-  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], one output per thread.
+  // X = G V^{-1}: X[i, q] = sum_p G[i, p] Vi[p, q], one output per thread
+  // (compensated: as accurate as a double-float evaluation).
   for (int t = tid; t < In * R; t += nt) {
     const int q = t / In, i = t - q * In;
     const float* g = Gs + i * RS;
     const df* vi = Vis + R * q;
-    df s0{0.f, 0.f}, s1{0.f, 0.f};
-    int p = 0;
-    for (; p + 1 < R; p += 2) {
-      s0 = df_add(s0, df_mul_f(vi[p], g[p]));
-      s1 = df_add(s1, df_mul_f(vi[p + 1], g[p + 1]));
-    }
-    if (p < R) s0 = df_add(s0, df_mul_f(vi[p], g[p]));
-    X[i * RS + q] = df_add(s0, s1);
+    dot2 acc;
+    for (int p = 0; p < R; ++p) acc.add_fd(g[p], vi[p]);
+    X[i * RS + q] = acc.value();
   }
   __syncthreads();
 
   // lambda_q = ||x_q||, a_q = x_q / lambda_q (1/lambda_q = rsqrt(||x_q||^2)), warp per column.
   for (int q = warp; q < R; q += nw) {
-    df s0{0.f, 0.f}, s1{0.f, 0.f};
-    int i = lane;
-    for (; i + 32 < In; i += 64) {
-      s0 = df_add(s0, df_mul(X[i * RS + q], X[i * RS + q]));
-      s1 = df_add(s1, df_mul(X[(i + 32) * RS + q], X[(i + 32) * RS + q]));
-    }
-    if (i < In) s0 = df_add(s0, df_mul(X[i * RS + q], X[i * RS + q]));
-    const df ss = df_warp_sum(df_add(s0, s1));
+    dot2 sq;
+    for (int i = lane; i < In; i += 32) sq.add_sq(X[i * RS + q]);
+    const df ss = df_warp_sum(sq.value());
     df lq, il;
     if (ss.hi > 0.f) {
       il = df_rsqrt(ss);
@@ -216,15 +223,16 @@ __device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
       lq = df{0.f, 0.f};
       il = df_make(1.f);
     }
-    df ip{0.f, 0.f};
+    dot2 ipa;
     for (int r = lane; r < In; r += 32) {
       const df v = df_mul(X[r * RS + q], il);
       const float f = __fadd_rn(v.hi, v.lo);
       a.An[r + In * q] = f;
       Fs[r * RS + q] = f;
-      if (want_fit) ip = df_add_prod_ff(ip, f, Gs[r * RS + q]);
+      if (want_fit) ipa.add_ff(f, Gs[r * RS + q]);
     }
-    if (want_fit) ip = df_warp_sum(ip);
+    df ip{0.f, 0.f};
+    if (want_fit) ip = df_warp_sum(ipa.value());
     if (lane == 0) {
       lam[q] = lq;
       part[q] = df_mul(lq, ip);
@@ -240,7 +248,7 @@ __device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
   for (int pq0 = 0; pq0 < npairs; pq0 += ngroups) {
     const int pq = pq0 + (tid >> 3);
     int p = 0, q = 0;
-    df s0{0.f, 0.f}, s1{0.f, 0.f};
+    dot2 acc;
     if (pq < npairs) {
       int rem = pq;
       while (rem >= R - p) {
@@ -248,14 +256,9 @@ __device__ void als_update_block(const AlsDfArgs& a, unsigned char* smraw) {
         ++p;
       }
       q = p + rem;
-      int i = sub;
-      for (; i + 8 < In; i += 16) {
-        s0 = df_add_prod_ff(s0, Fs[i * RS + p], Fs[i * RS + q]);
-        s1 = df_add_prod_ff(s1, Fs[(i + 8) * RS + p], Fs[(i + 8) * RS + q]);
-      }
-      if (i < In) s0 = df_add_prod_ff(s0, Fs[i * RS + p], Fs[i * RS + q]);
+      for (int i = sub; i < In; i += 8) acc.add_ff(Fs[i * RS + p], Fs[i * RS + q]);
     }
-    df s = df_add(s0, s1);
+    df s = acc.value();
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o, 8));
     if (pq < npairs && sub == 0) {

@@ -98,6 +98,40 @@ __device__ __forceinline__ df df_rcp(df a) {
   return quick_two_sum(y0, __fmul_rn(y0, e.hi));
 }
 
+// Compensated accumulation of a sum of products (Ogita, Rump, Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26, 2005, algorithm Dot2): each
+// product is split exactly by TwoProd, the running float sum s is advanced by
+// TwoSum, and every rounding error (of the products and of the additions) is
+// added into the float c.  The result s + c is as accurate as a dot product
+// evaluated in twice the working precision and then rounded; the dependent
+// chain through s is one addition per term (c never feeds back into s).
+struct dot2 {
+  float s = 0.f, c = 0.f;
+  // += a * b for floats a, b.
+  __device__ __forceinline__ void add_ff(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(es, ep));
+  }
+  // += a * b for a float a and a double-float b (a * b.lo, two orders below
+  // a * b.hi, goes into the error term by one fused multiply-add).
+  __device__ __forceinline__ void add_fd(float a, df b) {
+    add_ff(a, b.hi);
+    c = __fmaf_rn(a, b.lo, c);
+  }
+  // += x^2 for a double-float x (2 x.hi x.lo into the error term; x.lo^2 is
+  // below the result's precision).
+  __device__ __forceinline__ void add_sq(df x) {
+    add_ff(x.hi, x.hi);
+    c = __fmaf_rn(__fmul_rn(2.f, x.hi), x.lo, c);
+  }
+  __device__ __forceinline__ df value() const { return two_sum(s, c); }
+};
+
 __device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }
 
 __device__ __forceinline__ df df_from_double(double d) {
