@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "consumers.cuh"
 #include "lead_dispatch.cuh"
+#include "tensor_map.h"
 #include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
 
@@ -139,6 +140,10 @@ struct LeadPlan {
   int nJb = 0, nKs = 0;
   int64_t Kc = 0;
   size_t rpart_elems = 0, lpart_elems = 0;
+  // CUDA-core kernel: Khatri-Rao rows built once per pass (kr_rows_kernel).
+  int RT = 0;                 // the instance's rank tile (stored ranks per group)
+  bool wl_rank_major = false;
+  size_t wr_elems = 0, wl_elems = 0;
 };
 
 SimtShape shape_for(int prec, int r, int sides) {
@@ -298,6 +303,11 @@ LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
   choose_grid(p, R, is_f64(prec) ? 8 : 4, num_sms() * std::max(bps, 1));
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
   p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
+  // Built rows: every column chunk (W_R) / row tile of every J-block (W_L) a CTA reads.
+  p.RT = sh.RT;
+  p.wl_rank_major = sh.wl_rank_major;
+  p.wr_elems = (sh.wpre && (sides & 1)) ? size_t(p.groups) * p.RT * size_t((p.K + p.TK - 1) / p.TK * p.TK) : 0;
+  p.wl_elems = (sh.wpre && (sides & 2)) ? size_t(p.groups) * p.RT * size_t(p.nJb) * p.nrt * p.TJ : 0;
   return p;
 }
 
@@ -342,17 +352,22 @@ struct ChainBufs {
 
 // Kronecker tables of the leading pass's Khatri-Rao rows (modes (0, k) for
 // W_L and (k, N) for W_R; only needed when a run has three or more modes).
+// Built Khatri-Rao rows of the CUDA-core passes (sized by the plans a:, b:).
 template <typename T>
 struct LeadTabs {
   T* qL = nullptr;
   T* qR = nullptr;
+  T* wR = nullptr;
+  T* wL = nullptr;
 };
 
 template <typename T>
-LeadTabs<T> take_tabs(Carver& c, const Shape& s, int R, int k) {
+LeadTabs<T> take_tabs(Carver& c, const Shape& s, int R, int k, const LeadPlan& a, const LeadPlan& b) {
   LeadTabs<T> t;
   t.qL = c.take<T>(size_t(R) * (k >= 3 ? prod(s, 1, k) : 1));
   t.qR = c.take<T>(size_t(R) * (s.N - k >= 3 ? prod(s, k + 1, s.N) : 1));
+  t.wR = c.take<T>(std::max<size_t>(std::max(a.wr_elems, b.wr_elems), 1));
+  t.wL = c.take<T>(std::max<size_t>(std::max(a.wl_elems, b.wl_elems), 1));
   return t;
 }
 
@@ -398,7 +413,7 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
   w.Rpart = c.take<T>(std::max<size_t>(lp.rpart_elems, 1));
   w.Lpart = c.take<T>(std::max<size_t>(lp.lpart_elems, 1));
   w.ch = take_chain<T>(c, s, R, lp.J, lp.K, lp.k);
-  w.tabs = take_tabs<T>(c, s, R, lp.k);
+  w.tabs = take_tabs<T>(c, s, R, lp.k, lp, lp);
   if (bytes) *bytes = c.off;
   return w;
 }
@@ -445,7 +460,7 @@ ModeWs<T> carve_mode(void* base, const Shape& s, int R, int n, const ModeRoute& 
   w.part = c.take<T>(std::max<size_t>(rt.right ? rt.lead.rpart_elems : rt.lead.lpart_elems, 1));
   const int64_t len = rt.right ? prod(s, 0, n) : prod(s, n + 1, s.N);
   w.kr = c.take<T>(size_t(R) * len);
-  w.tabs = take_tabs<T>(c, s, R, rt.lead.k);
+  w.tabs = take_tabs<T>(c, s, R, rt.lead.k, rt.lead, rt.lead);
   if (bytes) *bytes = c.off;
   return w;
 }
@@ -479,7 +494,7 @@ AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const 
   w.grams = c.take<double>(size_t(s.N) * R * R);
   w.X = c.take<double>(size_t(imax) * R);
   w.G = c.take<T>(size_t(imax) * R);
-  w.tabs = take_tabs<T>(c, s, R, lr.k);
+  w.tabs = take_tabs<T>(c, s, R, lr.k, lr, ll);
   w.V = c.take<double>(size_t(R) * R);
   w.Vi = c.take<double>(size_t(R) * R);
   if (bytes) *bytes = c.off;
@@ -582,10 +597,38 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   a.Lpart = Lpart;
   a.status = g_status_ptr;
   // Every rank group runs the widest group's instance; ranks beyond R are masked.
-  const int RT = shape_for(prec, std::min(R, p.RTmax), p.sides).RT;
+  const int RT = p.RT;
+  // Khatri-Rao rows built once per pass when the tiles come by TMA (the
+  // kernel copies them with each tile); else every CTA generates its own.
+  const bool wpre = matrix_map_ok(Y, int(sizeof(T)), p.J, p.K) && ((p.sides & 1) == 0 || p.wr_elems > 0) &&
+                    ((p.sides & 2) == 0 || p.wl_elems > 0);
+  const int64_t kpad = (p.K + p.TK - 1) / p.TK * p.TK, jpad = int64_t(p.nJb) * p.nrt * p.TJ;
+  auto build = [&](T* dst, const KrRows<T>& kr, int64_t len, int64_t len_pad, int r0, int rank_major) {
+    ++g_launches;
+    Timed timer(st, kKindKron);
+    const int64_t total = len_pad * RT;
+    return launch_pdl(kr_rows_kernel<T>, dim3(blocks_for(total, 256, 2 * num_sms())), dim3(256), 0, st, dst, kr, len,
+                      len_pad, RT, r0, R, p.TJ, rank_major);
+  };
   for (int g = 0; g < p.groups; ++g) {
     a.r0 = g * p.RTmax;
     a.normpart = (g == 0) ? normpart : nullptr;
+    a.wpre_r = nullptr;
+    a.wpre_l = nullptr;
+    if (wpre) {
+      cudaError_t e = cudaSuccess;
+      if (p.sides & 1) {
+        T* d = tabs.wR + size_t(g) * RT * kpad;
+        e = build(d, a.wr, p.K, kpad, a.r0, 0);
+        a.wpre_r = d;
+      }
+      if (e == cudaSuccess && (p.sides & 2)) {
+        T* d = tabs.wL + size_t(g) * RT * jpad;
+        e = build(d, a.wl, p.J, jpad, a.r0, p.wl_rank_major ? 1 : 0);
+        a.wpre_l = d;
+      }
+      if (e != cudaSuccess) return e;
+    }
     cudaError_t e = launch_lead(a, RT, p.sides, dim3(p.nJb, p.nKs), st);
     if (e != cudaSuccess) return e;
   }
@@ -715,6 +758,15 @@ int choose_split(const Shape& s, const cpg_opts* opts) {
 }
 
 // ---- plan of the all-mode gradient: split k, one fused pass or two ----------------
+// One workspace layout for the two passes of a gradient: the R pass's plan
+// with the larger of the two passes' L-side buffers.
+LeadPlan grad_sizing(const LeadPlan& pr, const LeadPlan& pl) {
+  LeadPlan z = pr;
+  z.lpart_elems = std::max(pr.lpart_elems, pl.lpart_elems);
+  z.wl_elems = std::max(pr.wl_elems, pl.wl_elems);
+  return z;
+}
+
 struct GradChoice {
   int k = 1;
   bool fused = false;
@@ -723,7 +775,7 @@ struct GradChoice {
 // Workspace bytes of the all-mode gradient under plan c.
 size_t grad_bytes(const Shape& s, int R, int prec, const GradChoice& c) {
   LeadPlan pr = plan_lead(s, R, c.k, c.fused ? 3 : 1, prec);
-  if (!c.fused) pr.lpart_elems = std::max(pr.lpart_elems, plan_lead(s, R, c.k, 2, prec).lpart_elems);
+  if (!c.fused) pr = grad_sizing(pr, plan_lead(s, R, c.k, 2, prec));
   size_t bytes = 0;
   if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes);
   else carve_grad<float>(nullptr, s, R, pr, &bytes);
@@ -801,8 +853,7 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   LeadPlan pr = plan_lead(s, R, k, fused ? 3 : 1, o->precision);
   LeadPlan pl = fused ? pr : plan_lead(s, R, k, 2, o->precision);
   // Workspace: one layout sized for the larger of the two plans.
-  LeadPlan sizing = pr;
-  sizing.lpart_elems = std::max(pr.lpart_elems, pl.lpart_elems);
+  const LeadPlan sizing = grad_sizing(pr, pl);
   size_t need = 0;
   GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
   if (!lead_fits(pr) || !lead_fits(pl)) return CPG_ERR_UNSUPPORTED;

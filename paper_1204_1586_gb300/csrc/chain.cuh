@@ -33,12 +33,55 @@ struct FacArgs {
 
 template <typename T>
 __global__ void kr_build_kernel(T* __restrict__ out, const FacArgs<T> f, int mb, int me, int64_t len, int R) {
+  griddep_launch();  // the kernels that follow may start launching (they wait for this one)
   griddep_wait();
   const int64_t total = len * R;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     const int r = int(t / len);
     const int64_t o = t - int64_t(r) * len;
     out[t] = kr_entry<T>(f.A, f.I, mb, me, o, r);
+  }
+}
+
+// Khatri-Rao rows of a leading pass (W_R of eq. 3.10 or W_L of eq. 3.9), built
+// once per pass for one rank group (ranks r0 .. r0 + RT - 1) in the padded
+// layouts the CUDA-core leading kernel copies per stage (LeadArgs::wpre_r /
+// wpre_l):
+//   rank_major = 0: out[o * RT + r],                        o < len_pad
+//   rank_major = 1: out[(o / TJ) * RT * TJ + r * TJ + o % TJ]
+// Entry (o, r) is the factor row of the first mode times the Kronecker-table
+// entry of the others, the product the kernel would form itself (KrRows),
+// and zero for o >= len or r0 + r >= R.  The kernels that follow may launch
+// at once: they wait for this one before they read the rows.
+template <typename T>
+__global__ void kr_rows_kernel(T* __restrict__ out, const KrRows<T> kr, int64_t len, int64_t len_pad, int RT, int r0,
+                               int R, int TJ, int rank_major) {
+  griddep_launch();
+  griddep_wait();
+  const int64_t total = len_pad * RT, tile = int64_t(RT) * TJ;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    int64_t o;
+    int r;
+    if (rank_major) {
+      const int64_t tb = t / tile, w = t - tb * tile;
+      r = int(w / TJ);
+      o = tb * TJ + (w - int64_t(r) * TJ);
+    } else {
+      o = t / RT;
+      r = int(t - o * RT);
+    }
+    T v = T(0);
+    if (o < len && r0 + r < R) {
+      if (kr.A == nullptr) {
+        v = T(1);
+      } else {
+        const uint32_t q = kr.d.div(uint32_t(o)), i = uint32_t(o) - q * kr.d.d;
+        const T fa = kr.A[i + int64_t(kr.d.d) * (r0 + r)];
+        const T fq = (kr.Q != nullptr) ? kr.Q[q + kr.ldq * (r0 + r)] : T(1);
+        v = fa * fq;
+      }
+    }
+    out[t] = v;
   }
 }
 

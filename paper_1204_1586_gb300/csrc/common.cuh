@@ -82,6 +82,13 @@ struct LeadArgs {
   T* Lpart;                 // [nJb][R][K]  L-side partial sums (per J-block)
   double* normpart;         // [nJb*nKs] partial sums of y^2, or nullptr
   int use_tma;              // 1: tiles arrive by TMA (set by the launcher); 0: element copies
+  // Khatri-Rao rows built once per pass (kr_rows_kernel), copied per stage with
+  // the tile when tiles arrive by TMA; nullptr: each CTA generates its own.
+  //   wpre_r: [Kpad][RT]                 (column c, rank r at c * RT + r)
+  //   wpre_l: [J tiles][RT][TJ] if rank-major, else [J tiles][TJ][RT]
+  // for this launch's rank group, zero past K / J and past rank R.
+  const T* wpre_r;
+  const T* wpre_l;
   int* status;              // device status word (bounded-wait timeouts)
 };
 

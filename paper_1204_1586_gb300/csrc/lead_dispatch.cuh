@@ -9,6 +9,8 @@ namespace cpg {
 struct SimtShape {
   int RT, TJ, TK;
   size_t smem;
+  bool wl_rank_major;  // the instance's W_L rows are stored rank-major ([r][j])
+  bool wpre;           // the instance takes Khatri-Rao rows built once per pass
 };
 
 // Smallest supported rank tile >= r (r <= max tile), and the row tile TJ and

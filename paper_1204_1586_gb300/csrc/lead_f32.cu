@@ -61,7 +61,10 @@ template <int RT, int TJ, int TJL>
 SimtShape shape(int sides) {
   using C = SimtCfg<float, RT, TJ, 3>;
   using CL = SimtCfg<float, RT, TJL, 2>;
-  return sides == 2 ? SimtShape{RT, TJL, CL::TK, CL::smem_bytes} : SimtShape{RT, TJ, C::TK, C::smem_bytes};
+  using CR = SimtCfg<float, RT, TJ, 1>;
+  return sides == 2 ? SimtShape{RT, TJL, CL::TK, CL::smem_bytes, CL::LP, CL::WPRE}
+         : sides == 1 ? SimtShape{RT, TJ, CR::TK, CR::smem_bytes, CR::LP, CR::WPRE}
+                      : SimtShape{RT, TJ, C::TK, C::smem_bytes, C::LP, C::WPRE};
 }
 }  // namespace
 

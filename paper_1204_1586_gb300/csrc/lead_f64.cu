@@ -54,16 +54,20 @@ int bps_sides(int sides) {
 }
 
 template <int RT, int TJ>
-SimtShape shape() {
+SimtShape shape(int sides) {
   using C = SimtCfg<double, RT, TJ, 3>;
-  return SimtShape{RT, TJ, C::TK, C::smem_bytes};
+  using CR = SimtCfg<double, RT, TJ, 1>;
+  using CL = SimtCfg<double, RT, TJ, 2>;
+  return sides == 1 ? SimtShape{RT, TJ, CR::TK, CR::smem_bytes, CR::LP, CR::WPRE}
+         : sides == 2 ? SimtShape{RT, TJ, CL::TK, CL::smem_bytes, CL::LP, CL::WPRE}
+                      : SimtShape{RT, TJ, C::TK, C::smem_bytes, C::LP, C::WPRE};
 }
 }  // namespace
 
-SimtShape simt_shape_f64(int r, int) {
-  if (r <= 4) return shape<4, 128>();
-  if (r <= 8) return shape<8, 128>();
-  return shape<16, 64>();
+SimtShape simt_shape_f64(int r, int sides) {
+  if (r <= 4) return shape<4, 128>(sides);
+  if (r <= 8) return shape<8, 128>(sides);
+  return shape<16, 64>(sides);
 }
 
 int lead_blocks_per_sm_f64(int RT, int sides) {

@@ -93,8 +93,18 @@ struct SimtCfg {
   // when it fits there.
   static constexpr bool RED_ALIAS = size_t(WR) * RT * TK <= size_t(TK) * TJ;
   static constexpr size_t y_elems = size_t(STAGES) * TK * TJ;
-  static constexpr size_t wr_elems = DO_R ? size_t(2) * TK * RT : 0;
-  static constexpr size_t wl_elems = DO_L ? size_t(DO_R ? 1 : 2) * TJ * RT : 0;
+  // Khatri-Rao row buffers.  When a stage's rows are at most a quarter of its
+  // tile (WPRE), rows built once per pass (LeadArgs::wpre_r / wpre_l) come
+  // with each tile into a ring of STAGES slots; otherwise (and when no rows
+  // are built) the CTA writes slots 0 and 1 itself (one W_L slot when both
+  // sides run: W_L is then fixed per CTA).
+  static constexpr size_t wr_slot = size_t(TK) * RT, wl_slot = size_t(TJ) * RT;
+  static constexpr bool WPRE = 4 * ((DO_R ? wr_slot : 0) + (DO_L ? wl_slot : 0)) * sizeof(T) <= size_t(STAGE_BYTES);
+  static constexpr size_t wr_elems = DO_R ? size_t(WPRE ? STAGES : 2) * wr_slot : 0;
+  static constexpr size_t wl_elems = DO_L ? size_t(WPRE ? STAGES : DO_R ? 1 : 2) * wl_slot : 0;
+  static_assert(STAGES >= 2, "two Khatri-Rao slots at least");
+  static_assert((wr_slot * sizeof(T)) % 16 == 0 && (wl_slot * sizeof(T)) % 16 == 0,
+                "Khatri-Rao slots are whole 16-byte units (bulk copies)");
   static constexpr size_t red_elems = (DO_L && WR > 1 && !RED_ALIAS) ? size_t(WR) * RT * TK : 0;
   // + slack to align the tile ring to 1024 bytes (128-byte swizzle atoms).
   static constexpr size_t smem_bytes = (y_elems + wr_elems + wl_elems + red_elems) * sizeof(T) + 1024;
@@ -208,6 +218,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   T* WLs = WRs + C::wr_elems;
   T* red_sep = WLs + C::wl_elems;
   __shared__ uint64_t bar_full[STAGES];
+  __shared__ uint64_t bar_w;  // Khatri-Rao rows of the prologue stages (built rows only)
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -222,9 +233,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   const int nst = nchunk * nrt;
   const bool do_norm = DO_R && (a.normpart != nullptr);
   const bool use_tma = a.use_tma != 0;
+  // Khatri-Rao rows built once per pass arrive with the tiles (TMA mode only).
+  const bool wpre = C::WPRE && use_tma && (!DO_R || a.wpre_r != nullptr) && (!DO_L || a.wpre_l != nullptr);
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) tc::mbar_init(&bar_full[s], 1);
+    tc::mbar_init(&bar_w, 1);
     tc::mbar_fence_init();
     abort_flag = 0;
   }
@@ -235,6 +249,19 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   // it has landed".
   int issued = 0;               // stages issued so far
   int iss_ci = 0, iss_rt = 0;   // column chunk and row tile of stage `issued`
+  constexpr uint32_t WR_BYTES = uint32_t(C::wr_slot * sizeof(T)), WL_BYTES = uint32_t(C::wl_slot * sizeof(T));
+  constexpr uint32_t W_BYTES = (DO_R ? WR_BYTES : 0u) + (DO_L ? WL_BYTES : 0u);
+  // Built Khatri-Rao rows of stage s (column chunk ci, row tile rt) into ring slot s % STAGES.
+  auto load_w = [&](int s, int ci, int rt, uint64_t* bar) {
+    if constexpr (DO_R)
+      tc::bulk_load(WRs + size_t(s % STAGES) * C::wr_slot, a.wpre_r + (kbeg + int64_t(ci) * TK) * RT, WR_BYTES, bar);
+    if constexpr (DO_L)
+      tc::bulk_load(WLs + size_t(s % STAGES) * C::wl_slot, a.wpre_l + (int64_t(jb) * nrt + rt) * C::wl_slot, WL_BYTES,
+                    bar);
+  };
+  // The prologue stages are issued before the previous kernel's results are
+  // awaited: their Khatri-Rao rows follow on bar_w once it has completed.
+  bool w_with_tile = false;
   auto issue = [&](int it) {    // it == issued, or past the last stage
     if (it >= nst) {
       if (!use_tma) cp_async_commit();
@@ -244,6 +271,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     T* dst = Ys + size_t(it % STAGES) * TK * TJ;
     const int64_t cbase = kbeg + int64_t(iss_ci) * TK;
     const int64_t j0 = jblk + int64_t(iss_rt) * TJ;
+    const int ci_it = iss_ci, rt_it = iss_rt;
     if (++iss_rt == nrt) {
       iss_rt = 0;
       ++iss_ci;
@@ -252,10 +280,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       if (tid == 0) {
         tc::fence_async_smem();
         uint64_t* bar = &bar_full[it % STAGES];
-        tc::mbar_arrive_expect_tx(bar, uint32_t(C::STAGE_BYTES));
+        const bool w = wpre && w_with_tile;
+        tc::mbar_arrive_expect_tx(bar, uint32_t(C::STAGE_BYTES) + (w ? W_BYTES : 0u));
 #pragma unroll
         for (int s = 0; s < C::NSEG; ++s)
           tc::tma_load_2d(dst + s * TK * SEG, &tmap, int(j0) + s * SEG, int(cbase), bar);
+        if (w) load_w(it, ci_it, rt_it, bar);
       }
     } else {
 #pragma unroll 4
@@ -333,15 +363,32 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
 #pragma unroll 1
   for (int s = 0; s < STAGES - 1; ++s) issue(s);
   griddep_wait();
-  if constexpr (DO_L) {
-    fetch_wl(0);
-    store_wl(WLs);
+  w_with_tile = true;
+  if (wpre) {
+    if (tid == 0) {
+      const int np = (nst < STAGES - 1) ? nst : STAGES - 1;
+      tc::mbar_arrive_expect_tx(&bar_w, uint32_t(np) * W_BYTES);
+      int ci = 0, rt = 0;
+      for (int s = 0; s < np; ++s) {
+        load_w(s, ci, rt, &bar_w);
+        if (++rt == nrt) {
+          rt = 0;
+          ++ci;
+        }
+      }
+      if (!tc::mbar_wait(&bar_w, 0)) abort_flag = 1;
+    }
+  } else {
+    if constexpr (DO_L) {
+      fetch_wl(0);
+      store_wl(WLs);
+    }
+    if constexpr (DO_R) {
+      fetch_wr(0);
+      store_wr(0);
+    }
   }
-  if constexpr (DO_R) {
-    fetch_wr(0);
-    store_wr(0);
-  }
-  __syncthreads();  // first Khatri-Rao rows stored
+  __syncthreads();  // first Khatri-Rao rows stored or landed
 
   constexpr int NP = RT / 2;  // rank pairs (FP32)
   T racc[C::NLD][C::VECR][(DO_R && !C::F2) ? RT : 1];                          // FP64 accumulators
@@ -398,13 +445,15 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     issue(it + STAGES - 1);
     // Khatri-Rao rows of the next stage: loads now, products stored after this
     // stage's arithmetic (into the buffer the previous stage used).
-    if constexpr (DO_R) fetch_wr(it + 1);
-    if (wl_per_stage && it + 1 < nst) fetch_wl(rt + 1 == nrt ? 0 : rt + 1);
+    if (!wpre) {
+      if constexpr (DO_R) fetch_wr(it + 1);
+      if (wl_per_stage && it + 1 < nst) fetch_wl(rt + 1 == nrt ? 0 : rt + 1);
+    }
 
     T* Yst = Ys + size_t(it % STAGES) * TK * TJ;
     if constexpr (DO_R) {
       // Lane: RPL rows (one 16-byte chunk per load); pairs hold two ranks of a row.
-      const T* Wr = WRs + size_t(it & 1) * TK * RT;
+      const T* Wr = WRs + size_t(wpre ? it % STAGES : it & 1) * C::wr_slot;
 #pragma unroll 2
       for (int i = 0; i < C::CPW; ++i) {
         const int c = warp + 8 * i;
@@ -451,7 +500,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
     }
 
     if constexpr (DO_L) {
-      const T* Wl = WLs + (wl_per_stage ? size_t(it & 1) * TJ * RT : 0);
+      const T* Wl = WLs + (wpre ? size_t(it % STAGES) * C::wl_slot : wl_per_stage ? size_t(it & 1) * C::wl_slot : 0);
       // Lanes read 16-byte chunks of consecutive columns at the same rows: the
       // XOR permutation puts 8 consecutive columns on 8 distinct bank groups.
       if constexpr (C::LP) {
@@ -561,10 +610,12 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
         zero_lacc();
       }
     }
-    if constexpr (DO_R) {
-      if (it + 1 < nst) store_wr(it + 1);
+    if (!wpre) {
+      if constexpr (DO_R) {
+        if (it + 1 < nst) store_wr(it + 1);
+      }
+      if (wl_per_stage && it + 1 < nst) store_wl(WLs + size_t((it + 1) & 1) * C::wl_slot);
     }
-    if (wl_per_stage && it + 1 < nst) store_wl(WLs + size_t((it + 1) & 1) * TJ * RT);
     if (++rt == nrt) {
       rt = 0;
       ++ci;
@@ -580,6 +631,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
       // the newest phase of every stage buffer (older phases have completed).
       for (int q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
         tc::mbar_wait(&bar_full[q % STAGES], uint32_t(q / STAGES) & 1u, 1u << 16);
+      if (wpre) tc::mbar_wait(&bar_w, 0, 1u << 16);
     }
     return;
   }

@@ -27,6 +27,13 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // matrix read as zero.  False when TMA cannot address it: base not 16-byte
 // aligned, a column pitch that is not a multiple of 16 bytes, or extents
 // beyond 32-bit coordinates.
+// Whether a matrix of `rows` x `cols` elements (rows contiguous) at `base` has
+// the alignment and extents a tensor map needs.
+inline bool matrix_map_ok(const void* base, int esize, int64_t rows, int64_t cols) {
+  return (reinterpret_cast<uintptr_t>(base) % 16) == 0 && (rows * esize) % 16 == 0 && rows < (int64_t(1) << 31) &&
+         cols < (int64_t(1) << 31);
+}
+
 inline bool make_matrix_map(CUtensorMap* m, const void* base, CUtensorMapDataType dtype, int esize, int64_t rows,
                             int64_t cols, uint32_t box_rows, uint32_t box_cols, CUtensorMapSwizzle swizzle) {
   auto fn = tensor_map_encoder();
