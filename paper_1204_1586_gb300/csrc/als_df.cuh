@@ -68,15 +68,17 @@ __global__ void gram_all_df_kernel(const FacArgs<float> f, int R, df* grams) {
 }
 
 // ---- V and V^{-1} of one mode, by one block ----------------------------------------
-// V = Hadamard_{m != n} Gram_m into Vs and V^{-1} into Vis ([R][R], symmetric,
-// Vis[p + R q]), by Gauss-Jordan elimination of [V | I] in `work`
-// ((2 R^2 + 6 R) double-floats).  Step j touches only the R columns
-// j+1 .. R+j (earlier left columns are finished unit vectors, later right
-// columns are still identity columns) and reads row j and column j from side
-// buffers written by step j - 1, so every entry updates in place with one
-// barrier per step.  Returns false (on every thread) when a pivot is not
+// V = Hadamard_{m != n} Gram_m into V_out and V^{-1} into Vi_out ([R][R],
+// symmetric, Vi_out[p + R q]; global memory), by Gauss-Jordan elimination of
+// [V | I] in shared `work` ((2 R^2 + 6 R) double-floats).  Step j touches only
+// the R columns j+1 .. R+j (earlier left columns are finished unit vectors,
+// later right columns are still identity columns) and reads row j and column
+// j from side buffers written by step j - 1, so every entry updates in place
+// with one barrier per step; when the R x R active block fits the block's
+// threads each thread keeps its entry's row and column offset for all steps.
+// Returns false (on every thread, Vi_out unwritten) when a pivot is not
 // positive.
-__device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* Vs, df* Vis, df* work) {
+__device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* V_out, df* Vi_out, df* work) {
   const int R2 = 2 * R;
   df* M = work;            // [V | I], row-major: M[i * 2R + c]
   df* colb = M + R * R2;   // column j of M, two buffers of R
@@ -93,7 +95,7 @@ __device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* Vs, d
     for (int m = 0; m < kMaxOrder; ++m)
       if (m < N && m != n) v = df_mul(v, g[m]);
     const int i = t % R, c = t / R;  // V is symmetric: V[i][c]
-    Vs[t] = v;
+    V_out[t] = v;
     M[i * R2 + c] = v;
     M[i * R2 + R + c] = df_make(i == c ? 1.f : 0.f);
     if (c == 0) colb[i] = v;  // column 0 for step 0
@@ -104,6 +106,8 @@ __device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* Vs, d
   for (int j = tid; j < R; j += nt) rowb[(j & 1) * R2 + R + j] = df_make(1.f);
   __syncthreads();
 
+  const bool one = R * R <= nt;  // at most one active entry per thread
+  const int ei = tid / R, eo = tid - ei * R;
   for (int j = 0; j < R; ++j) {
     const df* col = colb + (j & 1) * R;
     const df* row = rowb + (j & 1) * R2;
@@ -112,20 +116,26 @@ __device__ bool df_inverse_block(const df* grams, int N, int n, int R, df* Vs, d
     const df p = col[j];
     if (!(p.hi > 0.f)) return false;  // every thread read the same pivot
     const df inv = df_rcp(p);
-    for (int e = tid; e < R * R; e += nt) {
-      const int i = e / R, c = j + 1 + (e - i * R);
+    auto step = [&](int i, int c) {
       const df v = (i == j) ? df_mul(row[c], inv) : df_sub(M[i * R2 + c], df_mul(df_mul(col[i], inv), row[c]));
       M[i * R2 + c] = v;
       if (c == j + 1) coln[i] = v;
       if (i == j + 1) rown[c] = v;
+    };
+    if (one) {
+      if (tid < R * R) step(ei, j + 1 + eo);
+    } else {
+      for (int e = tid; e < R * R; e += nt) {
+        const int i = e / R;
+        step(i, j + 1 + (e - i * R));
+      }
     }
     __syncthreads();
   }
   for (int t = tid; t < R * R; t += nt) {
     const int p = t % R, q = t / R;
-    Vis[t] = M[p * R2 + R + q];
+    Vi_out[t] = M[p * R2 + R + q];
   }
-  __syncthreads();
   return true;
 }
 
@@ -134,12 +144,12 @@ constexpr int kModeThreads = 512;
 
 // Shared memory of the update (V^{-1}, V, Gram_n, lambda, partials; then X
 // (double-float), G and the new factor (floats), all In x (R + 1)) and of the
-// inverse ([V | I], V, V^{-1} and the pivot row/column buffers); the mode
-// kernel takes the larger.
+// inverse ([V | I] and the pivot row/column buffers); the mode kernel takes
+// the larger.
 inline size_t als_df_smem_bytes(int64_t In, int R) {
   const size_t RS = size_t(R) + 1, R2 = size_t(R) * R;
   const size_t update = (3 * R2 + 2 * size_t(R)) * sizeof(df) + size_t(In) * RS * (sizeof(df) + 2 * sizeof(float));
-  const size_t inverse = (4 * R2 + 6 * size_t(R)) * sizeof(df);
+  const size_t inverse = (2 * R2 + 6 * size_t(R)) * sizeof(df);
   return (update > inverse ? update : inverse) + 16;
 }
 
@@ -307,14 +317,11 @@ __global__ void __launch_bounds__(kModeThreads) als_mode_df_kernel(const AlsMode
   if (blockIdx.x == gridDim.x - 1) {
     const AlsDfArgs& u = p.u;
     const int R = u.R;
-    df* Vs = reinterpret_cast<df*>(smraw);
-    df* Vis = Vs + R * R;
-    const bool ok = df_inverse_block(u.grams, u.N, u.n, R, Vs, Vis, Vis + R * R);
-    for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
-      u.V[t] = Vs[t];
-      u.Vi[t] = ok ? Vis[t] : df{0.f, 0.f};
+    const bool ok = df_inverse_block(u.grams, u.N, u.n, R, u.V, u.Vi, reinterpret_cast<df*>(smraw));
+    if (!ok) {
+      for (int t = threadIdx.x; t < R * R; t += blockDim.x) u.Vi[t] = df{0.f, 0.f};
+      if (threadIdx.x == 0) atomicCAS(u.status, 0, int(CPG_ERR_SINGULAR));
     }
-    if (!ok && threadIdx.x == 0) atomicCAS(u.status, 0, int(CPG_ERR_SINGULAR));
   } else if constexpr (LPO == 0) {
     seg_dot_tiled_run<float>(p.sd, blockIdx.x);
   } else {

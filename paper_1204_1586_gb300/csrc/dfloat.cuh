@@ -90,12 +90,22 @@ __device__ __forceinline__ df df_rsqrt(df a) {
   return quick_two_sum(y0, __fmul_rn(__fmul_rn(y0, e.hi), 0.5f));
 }
 
-// 1 / a for a != 0: correctly rounded FP32 reciprocal seed y0, then one Newton
-// step y = y0 + y0 (1 - a y0), the residual formed in double-float.
+// 1 / a for a normal, positive or negative (not zero, not subnormal): the
+// hardware's approximate reciprocal y0 of a.hi (relative error e ~ 2^-23),
+// then the Newton-Raphson correction carried to second order,
+//   1 / a = y0 / (1 - e) = y0 (1 + e + e^2 + ...),  e = 1 - a y0,
+// where e is formed by two fused multiply-adds (1 - a.hi y0 is exact in one
+// FMA because a.hi y0 is within 2^-22 of 1; a.lo y0 is then subtracted), so
+// the truncation is e^3 ~ 2^-69 and the result carries the double-float's
+// precision.  The dependent chain is one approximate reciprocal and five FP32
+// operations.
 __device__ __forceinline__ df df_rcp(df a) {
-  const float y0 = __frcp_rn(a.hi);
-  const df e = df_sub(df_make(1.f), df_mul_f(a, y0));
-  return quick_two_sum(y0, __fmul_rn(y0, e.hi));
+  float y0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(a.hi));
+  float e = __fmaf_rn(-a.hi, y0, 1.f);
+  e = __fmaf_rn(-a.lo, y0, e);
+  const float c = __fmaf_rn(e, e, e);  // e + e^2
+  return quick_two_sum(y0, __fmul_rn(y0, c));
 }
 
 // Compensated accumulation of a sum of products (Ogita, Rump, Oishi, "Accurate
