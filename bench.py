@@ -11,7 +11,9 @@ events on the launch stream between barriers.  e2e = the same metric with
 the tensor copied host->device and the results copied back inside every step.
 The roofline object reports the leading contraction (the kernel that streams
 Y, about 99% of the step's bytes): algorithmic bytes per launch = 4 * prod(I)
-over the event-timed duration of each of its launches in the timed region.
+over the event-timed duration of each of its launches, taken in a second run
+of the same K steps right after the timed one (events between kernels end the
+launch overlap of consecutive kernels, so they stay out of the step timing).
 
 --impl reference times the FP64 CPU oracle (explicit unfoldings and
 Khatri-Rao products, Algorithm 1 + eq. 2.14) on the same workload, a bounded
@@ -304,7 +306,6 @@ def main():
     clk.start()
     time.sleep(0.3)
     cg.launch_count(reset=True)
-    cg.profile_lead(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
@@ -314,6 +315,14 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     launches = cg.launch_count()
+    # The same K steps once more with every leading pass bracketed by CUDA
+    # events on its stream: the roofline's kernel durations.  An event between
+    # two kernels ends their launch overlap, so this region is not the step time.
+    cg.profile_lead(True)
+    barrier()
+    for _ in range(args.steps):
+        step(Y)
+    barrier()
     lead = cg.profile_read()
     cg.profile_lead(False)
     clocks = clk.stop()
