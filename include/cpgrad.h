@@ -278,6 +278,8 @@ int cpg_profile_lead(int enable);
 #define CPG_KIND_NORM 14        /* ||Y||^2                                      */
 #define CPG_KIND_UPDATE 15      /* CP_ALS update (FP64 data), NTF update        */
 #define CPG_KIND_MODEL_TERM 16  /* model term of eq. 2.13, step of eq. 2.15     */
+#define CPG_KIND_ROWS 17        /* Khatri-Rao rows of a leading pass (eq. 3.9 / 3.10), once per pass */
+#define CPG_KIND_PITCH 18       /* copy of Y_(1:k) with a 16-byte column pitch  */
 
 /* Waits for and returns the recorded launch durations in milliseconds
  * (ms[i]) and each launch's kind (sides[i], CPG_KIND_*), at most `max`

@@ -149,7 +149,8 @@ def launch_count(reset: bool = False) -> int:
 # Launch kinds of the timing record (cpgrad.h CPG_KIND_*).
 LAUNCH_KINDS = {1: "lead_step4_R", 2: "lead_step7_L", 3: "lead_step4+7_fused", 10: "chain_segmented_dot",
                 11: "als_mode_fused_update", 12: "gram", 13: "kronecker_vector", 14: "norm_y2",
-                15: "als_update_fp64_or_ntf", 16: "gradient_model_term"}
+                15: "als_update_fp64_or_ntf", 16: "gradient_model_term", 17: "khatri_rao_rows",
+                18: "pitched_copy_of_y"}
 
 
 def profile_lead(enable) -> None:

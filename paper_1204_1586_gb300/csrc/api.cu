@@ -47,7 +47,9 @@ enum LaunchKind : int {
   kKindKron = 13,    // Kronecker vector of a run of modes
   kKindNorm = 14,    // ||Y||^2 from partial sums
   kKindUpdate = 15,  // ALS update (FP64 data), multiplicative update (eq. 2.18)
-  kKindModelTerm = 16  // model term of the cost gradient (eq. 2.13) and first-order step (eq. 2.15)
+  kKindModelTerm = 16,  // model term of the cost gradient (eq. 2.13) and first-order step (eq. 2.15)
+  kKindRows = 17,       // Khatri-Rao rows of a CUDA-core leading pass, built once per pass
+  kKindPitch = 18       // copy of Y_(1:k) with a 16-byte column pitch
 };
 
 // Records a start event at construction and an end event at destruction when
@@ -396,6 +398,16 @@ struct GradLayout {
   size_t bytes = 0;
 };
 
+// Row pitch (elements) of a copy of Y_(1:k) whose columns start on 16-byte
+// boundaries, and its size; 0 when Y's own pitch J already does.
+int64_t pitched_ld(int64_t J, size_t esize) {
+  const int64_t q = int64_t(16 / esize);
+  return (J + q - 1) / q * q;
+}
+size_t pitched_elems(int64_t J, int64_t K, size_t esize) {
+  return (J * int64_t(esize)) % 16 == 0 ? 0 : size_t(pitched_ld(J, esize)) * size_t(K);
+}
+
 template <typename T>
 struct GradWs {
   Header h;
@@ -403,10 +415,11 @@ struct GradWs {
   T* Lpart;
   ChainBufs<T> ch;
   LeadTabs<T> tabs;
+  T* Yp;  // Y_(1:k) with a 16-byte column pitch (yp_elems > 0), last in the layout
 };
 
 template <typename T>
-GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size_t* bytes) {
+GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size_t* bytes, size_t yp_elems = 0) {
   Carver c(base);
   GradWs<T> w;
   w.h = take_header(c);
@@ -414,6 +427,7 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
   w.Lpart = c.take<T>(std::max<size_t>(lp.lpart_elems, 1));
   w.ch = take_chain<T>(c, s, R, lp.J, lp.K, lp.k);
   w.tabs = take_tabs<T>(c, s, R, lp.k, lp, lp);
+  w.Yp = yp_elems ? c.take<T>(yp_elems) : nullptr;
   if (bytes) *bytes = c.off;
   return w;
 }
@@ -478,10 +492,12 @@ struct AlsWs {
   LeadTabs<T> tabs;
   double* V;   // [R][R] V of the current mode (double-float pairs for FP32 data)
   double* Vi;  // [R][R] V^{-1}
+  T* Yp;       // Y_(1:k) with a 16-byte column pitch (yp_elems > 0), last in the layout
 };
 
 template <typename T>
-AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const LeadPlan& ll, size_t* bytes) {
+AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const LeadPlan& ll, size_t* bytes,
+                   size_t yp_elems = 0) {
   Carver c(base);
   AlsWs<T> w;
   w.h = take_header(c);
@@ -497,8 +513,25 @@ AlsWs<T> carve_als(void* base, const Shape& s, int R, const LeadPlan& lr, const 
   w.tabs = take_tabs<T>(c, s, R, lr.k, lr, ll);
   w.V = c.take<double>(size_t(R) * R);
   w.Vi = c.take<double>(size_t(R) * R);
+  w.Yp = yp_elems ? c.take<T>(yp_elems) : nullptr;
   if (bytes) *bytes = c.off;
   return w;
+}
+
+// Y_(1:k) into Yp with pitch pitched_ld(J): returns the tensor the leading
+// passes read and its pitch.
+template <typename T>
+const T* pitch_copy(const T* Y, T* Yp, int64_t J, int64_t K, int64_t* ldy, cudaStream_t st) {
+  if (Yp == nullptr) {
+    *ldy = J;
+    return Y;
+  }
+  *ldy = pitched_ld(J, sizeof(T));
+  ++g_launches;
+  Timed timer(st, kKindPitch);
+  launch_pdl(pitch_copy_kernel<T>, dim3(unsigned(std::min<int64_t>(K, int64_t(16) * num_sms()))), dim3(256), 0, st, Yp,
+             *ldy, Y, J, K);
+  return Yp;
 }
 
 // Streams of a device's pool for batched calls.
@@ -556,12 +589,14 @@ KrRows<T> make_rows(const Shape& s, const void* const* A, int R, int mb, int me,
 
 template <typename T>
 cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, const LeadPlan& p, T* Rpart, T* Lpart,
-                     double* normpart, int prec, const LeadTabs<T>& tabs, cudaStream_t st) {
+                     double* normpart, int prec, const LeadTabs<T>& tabs, cudaStream_t st, int64_t ldy = 0) {
+  if (ldy == 0) ldy = p.J;
   if constexpr (std::is_same_v<T, float>) {
     if (p.tc) {
       TcArgs a{};
       a.J = p.J;
       a.K = p.K;
+      a.ldy = ldy;
       a.R = R;
       if (p.sides & 2) a.wl = make_rows<float>(s, A, R, 0, p.k, tabs.qL, st);
       if (p.sides & 1) a.wr = make_rows<float>(s, A, R, p.k, s.N, tabs.qR, st);
@@ -588,6 +623,7 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   a.Y = Y;
   a.J = p.J;
   a.K = p.K;
+  a.ldy = ldy;
   a.R = R;
   if (p.sides & 2) a.wl = make_rows<T>(s, A, R, 0, p.k, tabs.qL, st);
   if (p.sides & 1) a.wr = make_rows<T>(s, A, R, p.k, s.N, tabs.qR, st);
@@ -600,12 +636,12 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   const int RT = p.RT;
   // Khatri-Rao rows built once per pass when the tiles come by TMA (the
   // kernel copies them with each tile); else every CTA generates its own.
-  const bool wpre = matrix_map_ok(Y, int(sizeof(T)), p.J, p.K) && ((p.sides & 1) == 0 || p.wr_elems > 0) &&
+  const bool wpre = matrix_map_ok(Y, int(sizeof(T)), p.J, p.K, ldy) && ((p.sides & 1) == 0 || p.wr_elems > 0) &&
                     ((p.sides & 2) == 0 || p.wl_elems > 0);
   const int64_t kpad = (p.K + p.TK - 1) / p.TK * p.TK, jpad = int64_t(p.nJb) * p.nrt * p.TJ;
   auto build = [&](T* dst, const KrRows<T>& kr, int64_t len, int64_t len_pad, int r0, int rank_major) {
     ++g_launches;
-    Timed timer(st, kKindKron);
+    Timed timer(st, kKindRows);
     const int64_t total = len_pad * RT;
     return launch_pdl(kr_rows_kernel<T>, dim3(blocks_for(total, 256, 2 * num_sms())), dim3(256), 0, st, dst, kr, len,
                       len_pad, RT, r0, R, p.TJ, rank_major);
@@ -776,9 +812,10 @@ struct GradChoice {
 size_t grad_bytes(const Shape& s, int R, int prec, const GradChoice& c) {
   LeadPlan pr = plan_lead(s, R, c.k, c.fused ? 3 : 1, prec);
   if (!c.fused) pr = grad_sizing(pr, plan_lead(s, R, c.k, 2, prec));
+  const size_t ypn = c.fused ? 0 : pitched_elems(pr.J, pr.K, is_f64(prec) ? 8 : 4);
   size_t bytes = 0;
-  if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes);
-  else carve_grad<float>(nullptr, s, R, pr, &bytes);
+  if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes, ypn);
+  else carve_grad<float>(nullptr, s, R, pr, &bytes, ypn);
   return bytes;
 }
 
@@ -854,15 +891,24 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   LeadPlan pl = fused ? pr : plan_lead(s, R, k, 2, o->precision);
   // Workspace: one layout sized for the larger of the two plans.
   const LeadPlan sizing = grad_sizing(pr, pl);
-  size_t need = 0;
-  GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need);
+  // Two passes over a tensor whose column pitch is not a multiple of 16
+  // bytes: a pitched copy (when the workspace holds it) lets both take TMA
+  // tiles, for one extra read and write of Y.
+  const size_t ypn = fused ? 0 : pitched_elems(pr.J, pr.K, sizeof(T));
+  size_t need = 0, need_copy = 0;
+  carve_grad<T>(nullptr, s, R, sizing, &need_copy, ypn);
+  const bool copy_y = ypn > 0 && o->workspace != nullptr && o->workspace_bytes >= need_copy;
+  GradWs<T> w = carve_grad<T>(o->workspace, s, R, sizing, &need, copy_y ? ypn : 0);
   if (!lead_fits(pr) || !lead_fits(pl)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
   g_status_ptr = w.h.status;
 
   // Steps 4 and 7: R^(k) and L^(k+1) from one read of Y (or two passes).
-  cudaError_t e = run_lead<T>(s, Y, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, w.tabs, st);
-  if (e == cudaSuccess && !fused) e = run_lead<T>(s, Y, A, R, pl, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st);
+  int64_t ldy = 0;
+  const T* Yl = pitch_copy<T>(Y, w.Yp, pr.J, pr.K, &ldy, st);
+  cudaError_t e = run_lead<T>(s, Yl, A, R, pr, w.Rpart, w.Lpart, nullptr, o->precision, w.tabs, st, ldy);
+  if (e == cudaSuccess && !fused)
+    e = run_lead<T>(s, Yl, A, R, pl, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st, ldy);
   if (e != cudaSuccess) return CPG_ERR_CUDA;
 
   // Right side: modes k-1, ..., 0 (steps 5, 11, 12; finishing contraction line 19).
@@ -1006,8 +1052,14 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
   const int k = choose_split(s, o);
   const LeadPlan lr = plan_lead(s, R, k, 1, o->precision);
   const LeadPlan ll = plan_lead(s, R, k, 2, o->precision);
-  size_t need = 0;
-  AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need);
+  // A copy of Y with a 16-byte column pitch when Y's own pitch is not one and
+  // the workspace holds it (cpg_workspace_size counts it): 2 * iters passes
+  // then take TMA tiles, for one extra read and write of Y.
+  const size_t ypn = pitched_elems(lr.J, lr.K, sizeof(T));
+  size_t need = 0, need_copy = 0;
+  carve_als<T>(nullptr, s, R, lr, ll, &need_copy, ypn);
+  const bool copy_y = ypn > 0 && o->workspace != nullptr && o->workspace_bytes >= need_copy;
+  AlsWs<T> w = carve_als<T>(o->workspace, s, R, lr, ll, &need, copy_y ? ypn : 0);
   if (!lead_fits(lr) || !lead_fits(ll)) return CPG_ERR_UNSUPPORTED;
   if (o->workspace == nullptr || o->workspace_bytes < need) return CPG_ERR_WORKSPACE;
   if (status_override) w.h.status = status_override;
@@ -1139,10 +1191,13 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     return p;
   };
 
+  int64_t ldy = 0;
+  const T* Yl = pitch_copy<T>(Y, w.Yp, lr.J, lr.K, &ldy, st);
   for (int it = 0; it < iters; ++it) {
     // Pass 1: R^(k) with the current trailing factors (step 4); modes k-1, ..., 0.
     double* np = (it == 0) ? w.normpart : nullptr;
-    if (run_lead<T>(s, Y, Ac, R, lr, w.Rpart, nullptr, np, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Yl, Ac, R, lr, w.Rpart, nullptr, np, o->precision, w.tabs, st, ldy) != cudaSuccess)
+      return CPG_ERR_CUDA;
     if (it == 0) {
       ++g_launches;
       Timed timer(st, kKindNorm);
@@ -1187,7 +1242,8 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       }
     }
     // Pass 2: L^(k+1) with the updated leading factors (step 7); modes k, ..., N-1.
-    if (run_lead<T>(s, Y, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st) != cudaSuccess) return CPG_ERR_CUDA;
+    if (run_lead<T>(s, Yl, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st, ldy) != cudaSuccess)
+      return CPG_ERR_CUDA;
     {
       const T* X = w.Lpart;
       int nparts = ll.nJb;
@@ -1322,8 +1378,9 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
     }
   } else if (call == CPG_CALL_ALS || call == CPG_CALL_NTF) {
     const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
-    if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes);
-    else carve_als<float>(nullptr, s, R, lr, ll, &bytes);
+    const size_t ypn = pitched_elems(lr.J, lr.K, is_f64(prec) ? 8 : 4);
+    if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes, ypn);
+    else carve_als<float>(nullptr, s, R, lr, ll, &bytes, ypn);
   } else {
     return 0;
   }

@@ -85,6 +85,21 @@ __global__ void kr_rows_kernel(T* __restrict__ out, const KrRows<T> kr, int64_t 
   }
 }
 
+// Y_(1:k) (J rows, pitch J) copied into a buffer whose columns start on
+// 16-byte boundaries (pitch ldd >= J), so that the leading passes can take TMA
+// tiles of a tensor whose own row pitch is not a multiple of 16 bytes.  The
+// rows J .. ldd-1 are never read (the tiles' out-of-range rows read as zero).
+template <typename T>
+__global__ void pitch_copy_kernel(T* __restrict__ dst, int64_t ldd, const T* __restrict__ src, int64_t J, int64_t K) {
+  griddep_wait();
+  for (int64_t c = blockIdx.x; c < K; c += gridDim.x) {
+    const T* s = src + J * c;
+    T* d = dst + ldd * c;
+#pragma unroll 8
+    for (int64_t j = threadIdx.x; j < J; j += blockDim.x) d[j] = s[j];
+  }
+}
+
 template <typename T>
 struct SegDot {
   const T* X;             // [nparts][R][S]

@@ -72,6 +72,7 @@ template <typename T>
 struct LeadArgs {
   const T* Y;
   int64_t J, K;
+  int64_t ldy;              // elements from one column of Y_(1:k) to the next (>= J)
   int R;                    // total rank
   int r0;                   // first rank column handled by this launch
   KrRows<T> wl;             // W_L rows: Khatri-Rao over modes [0, k)

@@ -16,7 +16,7 @@ cudaError_t run(const LeadArgs<float>& a, dim3 grid, cudaStream_t st) {
   CUtensorMap m{};
   LeadArgs<float> b = a;
   b.use_tma = make_matrix_map(&m, a.Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, int(sizeof(float)), a.J, a.K, uint32_t(C::SEG), uint32_t(C::TK),
-                              CU_TENSOR_MAP_SWIZZLE_128B)
+                              CU_TENSOR_MAP_SWIZZLE_128B, a.ldy)
                   ? 1
                   : 0;
   return launch_pdl(kern, grid, dim3(C::NT), C::smem_bytes, st, m, b);

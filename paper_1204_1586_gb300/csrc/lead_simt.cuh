@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
         const int c = f / TJ, j = f % TJ;
         const int64_t cg = cbase + c, jg = j0 + j;
         const bool in = cg < K && jg < J;
-        cp_async_zfill<int(sizeof(T))>(dst + tile_off<TK, SEG, VEC>(c, j), in ? a.Y + jg + J * cg : a.Y,
+        cp_async_zfill<int(sizeof(T))>(dst + tile_off<TK, SEG, VEC>(c, j), in ? a.Y + jg + a.ldy * cg : a.Y,
                                        in ? int(sizeof(T)) : 0);
       }
       cp_async_commit();

@@ -10,8 +10,8 @@ namespace cpg {
 namespace {
 
 // Y as a 2-D tensor [K][J] (J contiguous); one box = 128 rows x 64 columns.
-bool make_y_map(CUtensorMap* m, const float* Y, int64_t J, int64_t K) {
-  return make_matrix_map(m, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J, K, 128, 64, CU_TENSOR_MAP_SWIZZLE_NONE);
+bool make_y_map(CUtensorMap* m, const float* Y, int64_t J, int64_t K, int64_t ldy) {
+  return make_matrix_map(m, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J, K, 128, 64, CU_TENSOR_MAP_SWIZZLE_NONE, ldy);
 }
 
 template <int RTP, int SIDES, int PREC>
@@ -56,7 +56,7 @@ cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, 
   CUtensorMap m{};
   TcArgs b = a;
   b.Y = Y;
-  b.use_tma = make_y_map(&m, Y, a.J, a.K) ? 1 : 0;  // else element copies (rows not 16-byte aligned)
+  b.use_tma = make_y_map(&m, Y, a.J, a.K, a.ldy) ? 1 : 0;  // else element copies (rows not 16-byte aligned)
   switch (RTP) {
     case 16: return run_prec<16>(m, b, sides, prec, grid, st);
     case 32: return run_prec<32>(m, b, sides, prec, grid, st);

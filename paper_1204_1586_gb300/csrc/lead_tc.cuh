@@ -53,6 +53,7 @@ struct TcArgs {
   double* normpart;  // [nJb*nKs] partial sums of y^2 (R side only), or nullptr
   int* status;
   const float* Y;  // the tensor (element copies when use_tma == 0)
+  int64_t ldy;     // elements from one column of Y_(1:k) to the next (>= J)
   int use_tma;     // 1: TMA boxes; 0: every thread copies elements (rows not 16-byte aligned)
 };
 
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
       const int c = f >> 7, j = f & 127;
       const int64_t cg = cb + c, jg = j0 + j;
       const bool in = cg < K && jg < J;
-      cp_async_zfill4(dst + (c >> 6) * C::HALF + (c & 63) * 512 + j * 4, in ? a.Y + jg + J * cg : a.Y, in ? 4 : 0);
+      cp_async_zfill4(dst + (c >> 6) * C::HALF + (c & 63) * 512 + j * 4, in ? a.Y + jg + a.ldy * cg : a.Y, in ? 4 : 0);
     }
     tc::cp_async_mbar_arrive(&bar_full[b]);
   };

@@ -20,7 +20,7 @@ cudaError_t run(const TcArgs& a, dim3 grid, cudaStream_t st) {
   // Box = {32 rows (128 bytes), TKS columns}, 128-byte swizzle; element copies
   // into the same layout when rows are not whole 16-byte chunks.
   b.use_tma = make_matrix_map(&m, a.Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.J, a.K, 32, uint32_t(C::TKS),
-                              CU_TENSOR_MAP_SWIZZLE_128B)
+                              CU_TENSOR_MAP_SWIZZLE_128B, a.ldy)
                   ? 1
                   : 0;
   auto kern = lead_tf32_kernel<RTP, SIDES>;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256, 1) lead_tf32_kernel(const __grid_constant
       const int c = f / C::TJS, j = f % C::TJS;
       const int64_t cg = cb + c, jg = j0 + j;
       const bool in = cg < K && jg < J;
-      cp_async_zfill4(dst + tf32_tile_off<C::TKS>(j, c), in ? a.Y + jg + J * cg : a.Y, in ? 4 : 0);
+      cp_async_zfill4(dst + tf32_tile_off<C::TKS>(j, c), in ? a.Y + jg + a.ldy * cg : a.Y, in ? 4 : 0);
     }
     tc::cp_async_mbar_arrive(&bar_full[b]);
   };

@@ -63,6 +63,7 @@ GRAD_CASES = [
     ([13, 7, 9, 11], 8, "fp64"),
     ([21, 22, 23], 16, "fp64"),
     ([5, 6, 7], 20, "fp64"),            # two rank groups in FP64
+    ([20, 22, 23], 20, "fp64"),         # two rank groups, J=20: TMA tiles with built Khatri-Rao rows
     # split-BF16 forms on the tensor cores (TMA boxes when J * 4 is a multiple
     # of 16, element copies otherwise)
     ([24, 20, 30, 17], 12, "bf16x3"),   # k=2, J=480: ragged row tile and column chunk
