@@ -671,6 +671,23 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
   return cudaSuccess;
 }
 
+// The leading pass's partial sums, when there are enough of them, summed by
+// a grid over the whole GPU before the chain: the first finishing contraction
+// would otherwise add them up itself with a grid sized by its few outputs
+// (15 x R at 15^7, where that took 150 us of a 470 us sweep).  Returns the
+// tensor the chain reads and sets *nparts to 1, or leaves both unchanged.
+constexpr int64_t kPresumMin = int64_t(1) << 20;  // elements read (all parts)
+
+template <typename T>
+const T* presum_parts(const T* X, int* nparts, int64_t n, T* out, cudaStream_t st) {
+  if (*nparts <= 1 || int64_t(*nparts) * n < kPresumMin) return X;
+  ++g_launches;
+  Timed timer(st, kKindChain);
+  launch_pdl(sum_parts_kernel<T>, dim3(blocks_for(n, 256, 8 * num_sms())), dim3(256), 0, st, out, X, *nparts, n, n);
+  *nparts = 1;
+  return out;
+}
+
 // Lanes per output of a segmented dot product of reduction length `inner`.
 inline int seg_lanes(int64_t inner) { return inner >= 96 ? 32 : inner >= 24 ? 8 : inner >= 4 ? 4 : 1; }
 
@@ -913,11 +930,11 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
 
   // Right side: modes k-1, ..., 0 (steps 5, 11, 12; finishing contraction line 19).
   {
-    const T* X = w.Rpart;
     int nparts = pr.nKs;
     const int64_t pstride = int64_t(R) * pr.J;
     T* bufs[2] = {w.ch.Pa, w.ch.Pb};
     int cur = 0;
+    const T* X = presum_parts<T>(w.Rpart, &nparts, pstride, bufs[cur], st);
     for (int n = k; n >= 1; --n) {
       const int m = n - 1;
       const int64_t len_o = prod(s, 0, m), In = s.I[m];
@@ -936,11 +953,11 @@ cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, i
   }
   // Left side: modes k, ..., N-1 (steps 8, 15, 16; finishing contraction line 20).
   {
-    const T* X = w.Lpart;
     int nparts = pl.nJb;
     const int64_t pstride = int64_t(R) * pl.K;
     T* bufs[2] = {w.ch.Qa, w.ch.Qb};
     int cur = 0;
+    const T* X = presum_parts<T>(w.Lpart, &nparts, pstride, bufs[cur], st);
     for (int n = k; n < s.N; ++n) {
       const int64_t len_o = prod(s, n + 1, s.N), In = s.I[n];
       const T* kr = kr_vector<T>(s, A, R, n + 1, s.N, w.ch.kr, st);
@@ -1204,11 +1221,11 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
       launch_pdl(sum_norm_kernel, dim3(1), dim3(256), 0, st, w.normpart, int64_t(lr.nJb) * lr.nKs, w.h.normY2);
     }
     {
-      const T* X = w.Rpart;
       int nparts = lr.nKs;
       const int64_t pstride = int64_t(R) * lr.J;
       T* bufs[2] = {w.ch.Pa, w.ch.Pb};
       int cur = 0;
+      const T* X = presum_parts<T>(w.Rpart, &nparts, pstride, bufs[cur], st);
       bool g_done = false;  // this mode's update already ran (fused with the recursion)
       for (int n = k; n >= 1; --n) {
         const int m = n - 1;
@@ -1245,11 +1262,11 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
     if (run_lead<T>(s, Yl, Ac, R, ll, nullptr, w.Lpart, nullptr, o->precision, w.tabs, st, ldy) != cudaSuccess)
       return CPG_ERR_CUDA;
     {
-      const T* X = w.Lpart;
       int nparts = ll.nJb;
       const int64_t pstride = int64_t(R) * ll.K;
       T* bufs[2] = {w.ch.Qa, w.ch.Qb};
       int cur = 0;
+      const T* X = presum_parts<T>(w.Lpart, &nparts, pstride, bufs[cur], st);
       bool g_done = false;
       auto fit_of = [&](int n) { return (n == s.N - 1 && fit) ? fit + it : nullptr; };
       for (int n = k; n < s.N; ++n) {

@@ -116,6 +116,27 @@ struct SegDot {
   int R;
 };
 
+// X[0] + X[1] + ... + X[nparts-1] (the partial sums of a leading pass,
+// `stride` elements apart, n elements each) into out by a grid over the whole
+// GPU, added exactly as the segmented dot products below add them (from zero,
+// in the order q = 0, 1, ..., in batches of 8), so the chain's results do not
+// change when it reads the sum instead of the parts.
+template <typename T>
+__global__ void sum_parts_kernel(T* __restrict__ out, const T* __restrict__ X, int nparts, int64_t stride, int64_t n) {
+  griddep_wait();
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    T x = T(0);
+    for (int q0 = 0; q0 < nparts; q0 += 8) {
+      T v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = (q0 + e < nparts) ? X[(q0 + e) * stride + t] : T(0);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x += v[e];
+    }
+    out[t] = x;
+  }
+}
+
 // LPO lanes cooperate on one output; lanes stride the reduction index.  The
 // partial sums of an element are loaded in batches of 8 ahead of their
 // additions (which keep the fixed order q = 0, 1, ...), so that the loads
