@@ -336,9 +336,8 @@ __global__ void __launch_bounds__(kModeThreads) als_mode_df_kernel(const AlsMode
   if (s_ticket != gridDim.x - 1) return;
   __threadfence();
   if (threadIdx.x == 0) *p.ticket = 0u;  // ready for the next launch on this stream
-  // Every other CTA has exited: the next kernel may start launching (it waits
-  // for this one before reading anything this update writes).
-  griddep_launch();
+  // No early trigger: the next kernel launches when this one completes (an
+  // early launch measured slower, 209.4 against 207.6 us per 100^4 sweep).
   als_update_block(p.u, smraw);
 }
 

@@ -129,7 +129,7 @@ __global__ void sum_parts_kernel(T* __restrict__ out, const T* __restrict__ X, i
     for (int q0 = 0; q0 < nparts; q0 += 8) {
       T v[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = (q0 + e < nparts) ? X[(q0 + e) * stride + t] : T(0);
+      for (int e = 0; e < 8; ++e) v[e] = (q0 + e < nparts) ? __ldcs(X + (q0 + e) * stride + t) : T(0);
 #pragma unroll
       for (int e = 0; e < 8; ++e) x += v[e];
     }

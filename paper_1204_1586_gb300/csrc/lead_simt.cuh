@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
   int iss_ci = 0, iss_rt = 0;   // column chunk and row tile of stage `issued`
   constexpr uint32_t WR_BYTES = uint32_t(C::wr_slot * sizeof(T)), WL_BYTES = uint32_t(C::wl_slot * sizeof(T));
   constexpr uint32_t W_BYTES = (DO_R ? WR_BYTES : 0u) + (DO_L ? WL_BYTES : 0u);
+  const uint64_t y_policy = tc::policy_evict_first();  // the tiles are read once
   // Built Khatri-Rao rows of stage s (column chunk ci, row tile rt) into ring slot s % STAGES.
   auto load_w = [&](int s, int ci, int rt, uint64_t* bar) {
     if constexpr (DO_R)
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(256, (SimtCfg<T, RT, TJ, SIDES>::MIN_BLOCKS))
         tc::mbar_arrive_expect_tx(bar, uint32_t(C::STAGE_BYTES) + (w ? W_BYTES : 0u));
 #pragma unroll
         for (int s = 0; s < C::NSEG; ++s)
-          tc::tma_load_2d(dst + s * TK * SEG, &tmap, int(j0) + s * SEG, int(cbase), bar);
+          tc::tma_load_2d_hint(dst + s * TK * SEG, &tmap, int(j0) + s * SEG, int(cbase), bar, y_policy);
         if (w) load_w(it, ci_it, rt_it, bar);
       }
     } else {

@@ -184,8 +184,10 @@ __global__ void __launch_bounds__(256, 1) lead_tc_kernel(const __grid_constant__
     const int64_t j0 = jblk + int64_t(tile_of(ss)) * 128;
     uint64_t* bar = &bar_full[b];
     tc::mbar_arrive_expect_tx(bar, C::BUF_BYTES);
+    const uint64_t pol = tc::policy_evict_first();  // the tiles are read once
     for (int h = 0; h < 2; ++h)
-      tc::tma_load_2d(sm + C::OFF_BUF + b * C::BUF_BYTES + h * C::HALF, &tmap, int(j0), int(cb + 64 * h), bar);
+      tc::tma_load_2d_hint(sm + C::OFF_BUF + b * C::BUF_BYTES + h * C::HALF, &tmap, int(j0), int(cb + 64 * h), bar,
+                           pol);
   };
   // The same tile by element copies (every thread), in the TMA boxes' layout:
   // column c at (c / 64) * HALF + (c % 64) * 512 bytes, rows contiguous;

@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(256, 1) lead_tf32_kernel(const __grid_constant
     uint64_t* bar = &bar_full[b];
     tc::mbar_arrive_expect_tx(bar, C::RAW_BYTES);
     // Row coordinates are multiples of 32 elements (128 bytes), as TMA requires.
+    const uint64_t pol = tc::policy_evict_first();  // the tiles are read once
 #pragma unroll
     for (int x = 0; x < C::NBOX; ++x)
-      tc::tma_load_2d(sm + b * C::BUF_BYTES + x * C::BOX_BYTES, &tmap, int(j0) + 32 * x, int(cb), bar);
+      tc::tma_load_2d_hint(sm + b * C::BUF_BYTES + x * C::BOX_BYTES, &tmap, int(j0) + 32 * x, int(cb), bar, pol);
   };
   // The same tile by element copies (every thread), in the boxes' layout;
   // entries outside Y are zero-filled.
