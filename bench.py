@@ -576,11 +576,17 @@ def run_batched(args):
 
 
 def lead_kernel_hash(kernel):
+    """Hash of the kernel family's sources with comments and blank space
+    removed: it changes when the code does, not when a comment does."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in LEAD_KERNELS[kernel][0]:
-        with open(os.path.join(ROOT, "paper_1204_1586_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1204_1586_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -9,10 +9,12 @@
 //   L-side (step 7, eq. 3.9):   L^(k+1)[r, c] = sum_j W_L[j, r] * Y[j, c],
 //       W_L = A^(k) (.) ... (.) A^(1)     (Khatri-Rao over the leading modes)
 //
-// so that the all-mode gradient streams Y from memory once.  The Khatri-Rao
-// rows are generated per tile in shared memory (one factor row times one
-// entry of a small Kronecker table, eq. 3.3) and never materialised in
-// global memory.
+// so that the all-mode gradient streams Y from memory once.  Each Khatri-Rao
+// row is one factor row times one entry of a small Kronecker table (eq. 3.3).
+// Where a stage's rows are at most a quarter of its tile (WPRE) and the tiles
+// come by TMA, W_R and W_L are built once per pass in global memory
+// (kr_rows_kernel, 0.4 MB each at 100^4 R=10) and copied with every tile;
+// otherwise each CTA generates its rows per stage in shared memory.
 //
 // Work split: CTA (jb, ks) owns the J-block of nrt row tiles
 // [jb*nrt*TJ, (jb+1)*nrt*TJ) and the column range [ks*Kc, ks*Kc+Kc); stage s
@@ -21,10 +23,11 @@
 // nrt = 1; the L side alone may use tall blocks (nrt > 1) to cut the number
 // of J-block partials.
 //
-// Tiles arrive through a ring of STAGES buffers.  When rows are whole 16-byte
-// chunks one thread issues TMA copies (cp.async.bulk.tensor, 128-byte
-// swizzle) per stage; otherwise all threads issue element copies (cp.async
-// with zero fill) into the same layout.  Entries outside Y read as zero, and
+// Tiles arrive through a ring of STAGES buffers.  When columns start on
+// 16-byte boundaries (a.ldy, the column pitch, may exceed J for a pitched copy
+// of Y) one thread issues TMA copies (cp.async.bulk.tensor, 128-byte swizzle,
+// L2 evict-first: the tensor is read once) per stage; otherwise all threads
+// issue element copies (cp.async with zero fill) into the same layout.  Entries outside Y read as zero, and
 // Khatri-Rao rows outside Y are zero, so the arithmetic needs no bounds tests.
 // The layout (tile_off) stores each 128-byte run of a column as one line whose
 // 16-byte chunks are XOR-permuted by the column index, which serves both access
