@@ -7,6 +7,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -61,6 +62,29 @@ def test_workspace_size(L):
     a = cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
     b = cpgrad.cpg_workspace_size([100] * 4, 20, "fp32", 0, cpgrad.CALL_GRADIENT_ALL)
     assert 0 < a < 4e8 and 0 < b < 4e8
+
+
+def test_workspace_counts_pitched_copy(L):
+    """A tensor whose column pitch J is not a multiple of 16 bytes gets room for
+    a copy of Y with a padded pitch (ALS and the two-pass gradient); one whose
+    pitch already is does not."""
+    for prec, esize in (("fp32", 4), ("fp64", 8)):
+        q = 16 // esize
+        for I, k in (([15] * 5, 2), ([9, 11, 13, 7], 1), ([13, 7, 9, 11], 1)):
+            J = int(np.prod(I[:k]))
+            K = int(np.prod(I[k:]))
+            assert (J * esize) % 16 != 0
+            copy = (J + q - 1) // q * q * K * esize
+            for call in (cpgrad.CALL_ALS, cpgrad.CALL_GRADIENT_ALL):
+                odd = cpgrad.cpg_workspace_size(I, 8, prec, k, call)
+                assert odd >= copy, (I, prec, call)
+        # the same sizes with an aligned pitch need no copy: scratch far below the tensor
+        for call in (cpgrad.CALL_ALS, cpgrad.CALL_GRADIENT_ALL):
+            even = cpgrad.cpg_workspace_size([16] * 5, 8, prec, 2, call)
+            assert 0 < even < 16 ** 5 * esize, (prec, call)
+    # a single fused pass (FP32 at rank <= 4 fuses here) reads Y once: no copy
+    fused = cpgrad.cpg_workspace_size([15] * 5, 2, "fp32", 2, cpgrad.CALL_GRADIENT_ALL)
+    assert fused < 15 ** 5 * 4
 
 
 def _opts(prec=0, split=0, ws=None, nbytes=0):
