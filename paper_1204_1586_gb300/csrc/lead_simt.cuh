@@ -96,13 +96,13 @@ struct SimtCfg {
   // when it fits there.
   static constexpr bool RED_ALIAS = size_t(WR) * RT * TK <= size_t(TK) * TJ;
   static constexpr size_t y_elems = size_t(STAGES) * TK * TJ;
-  // Khatri-Rao row buffers.  When a stage's rows are at most a quarter of its
+  // Khatri-Rao row buffers.  When a stage's rows are at most half of its
   // tile (WPRE), rows built once per pass (LeadArgs::wpre_r / wpre_l) come
   // with each tile into a ring of STAGES slots; otherwise (and when no rows
   // are built) the CTA writes slots 0 and 1 itself (one W_L slot when both
   // sides run: W_L is then fixed per CTA).
   static constexpr size_t wr_slot = size_t(TK) * RT, wl_slot = size_t(TJ) * RT;
-  static constexpr bool WPRE = 4 * ((DO_R ? wr_slot : 0) + (DO_L ? wl_slot : 0)) * sizeof(T) <= size_t(STAGE_BYTES);
+  static constexpr bool WPRE = 2 * ((DO_R ? wr_slot : 0) + (DO_L ? wl_slot : 0)) * sizeof(T) <= size_t(STAGE_BYTES);
   static constexpr size_t wr_elems = DO_R ? size_t(WPRE ? STAGES : 2) * wr_slot : 0;
   static constexpr size_t wl_elems = DO_L ? size_t(WPRE ? STAGES : DO_R ? 1 : 2) * wl_slot : 0;
   static_assert(STAGES >= 2, "two Khatri-Rao slots at least");
