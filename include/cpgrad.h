@@ -102,7 +102,14 @@ int cpg_split_point(const int64_t* I, int N);
 
 /* Bytes of device workspace that `call` needs for this shape, rank and
  * options (opts->precision and opts->split are read; NULL opts = defaults).
- * Host-only.  Returns 0 on invalid arguments. */
+ * Host-only.  Returns 0 on invalid arguments.
+ * When the column pitch of reshape(Y, [J_k, K_k]) (J_k times the element
+ * size) is not a multiple of 16 bytes, the sizes for CP_ALS (CPG_CALL_ALS,
+ * CPG_CALL_NTF) and for a gradient that reads Y twice include a copy of Y
+ * with the pitch rounded up to 16 bytes: those calls copy Y once and stream
+ * the copy with TMA tiles.  Given a smaller workspace that still holds
+ * everything else, they skip the copy and stream Y itself with element copies
+ * (same results, about half the bandwidth). */
 size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call);
 
 /* All-mode CP gradient, Algorithm 2 (Section 3.3): G[n] <- Y_(n) KR_{m != n}
