@@ -310,8 +310,10 @@ int cpg_profile_read(float* ms, int* sides, int max);
  * precision and split are as in cpg_opts; stream is a cudaStream_t (NULL =
  * legacy default stream).
  *  - Returns CPG_ERR_WORKSPACE when cpg_workspace_size(I, N, R, ...,
- *    CPG_CALL_GRADIENT_ALL) exceeds CPG_NOALLOC_WORKSPACE_BYTES, and the
- *    argument errors of cp_gradient_all otherwise; nothing is launched then.
+ *    CPG_CALL_GRADIENT_ALL), less the optional pitched copy of Y it may
+ *    include, exceeds CPG_NOALLOC_WORKSPACE_BYTES (without room for the copy
+ *    the gradient streams Y itself), and the argument errors of
+ *    cp_gradient_all otherwise; nothing is launched then.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
  *    stream capture.

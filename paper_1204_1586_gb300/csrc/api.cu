@@ -16,6 +16,7 @@
 #include "consumers.cuh"
 #include "lead_dispatch.cuh"
 #include "tensor_map.h"
+#include "api_internal.h"
 #include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
 
@@ -826,10 +827,10 @@ struct GradChoice {
 };
 
 // Workspace bytes of the all-mode gradient under plan c.
-size_t grad_bytes(const Shape& s, int R, int prec, const GradChoice& c) {
+size_t grad_bytes(const Shape& s, int R, int prec, const GradChoice& c, bool with_copy = true) {
   LeadPlan pr = plan_lead(s, R, c.k, c.fused ? 3 : 1, prec);
   if (!c.fused) pr = grad_sizing(pr, plan_lead(s, R, c.k, 2, prec));
-  const size_t ypn = c.fused ? 0 : pitched_elems(pr.J, pr.K, is_f64(prec) ? 8 : 4);
+  const size_t ypn = (c.fused || !with_copy) ? 0 : pitched_elems(pr.J, pr.K, is_f64(prec) ? 8 : 4);
   size_t bytes = 0;
   if (is_f64(prec)) carve_grad<double>(nullptr, s, R, pr, &bytes, ypn);
   else carve_grad<float>(nullptr, s, R, pr, &bytes, ypn);
@@ -1353,17 +1354,8 @@ bool ptrs_ok(const void* const* P, int N) {
   return true;
 }
 
-}  // namespace
-
-extern "C" {
-
-int cpg_split_point(const int64_t* I, int N) {
-  Shape s;
-  if (check_shape(I, N, 1, s) != CPG_OK) return 0;
-  return split_point(s);
-}
-
-size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call) {
+// Workspace bytes of `call`; with_copy: including the optional pitched copy of Y.
+size_t workspace_size_impl(const int64_t* I, int N, int R, const cpg_opts* opts, int call, bool with_copy) {
   Shape s;
   if (check_shape(I, N, R, s) != CPG_OK) return 0;
   const int prec = opts ? opts->precision : CPG_FP32;
@@ -1375,16 +1367,16 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
   if (opts) od = *opts;
   od.precision = prec;
   if (call == CPG_CALL_GRADIENT_ALL) {
-    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od));
+    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od), with_copy);
     GradChoice t;
-    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t));
+    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t, with_copy));
   } else if (call == CPG_CALL_GRADIENT_FULL) {
-    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od));
+    bytes = grad_bytes(s, R, prec, default_choice(s, R, &od), with_copy);
     GradChoice t;
-    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t));
+    if (tuned_choice(s, R, &od, &t)) bytes = std::max(bytes, grad_bytes(s, R, prec, t, with_copy));
     bytes = align_up(bytes) + grams_bytes(N, R) + kAlign;
   } else if (call == CPG_CALL_GRADIENT_TUNE) {
-    for (const GradChoice& c : grad_candidates(s, R, &od)) bytes = std::max(bytes, grad_bytes(s, R, prec, c));
+    for (const GradChoice& c : grad_candidates(s, R, &od)) bytes = std::max(bytes, grad_bytes(s, R, prec, c, with_copy));
   } else if (call == CPG_CALL_GRADIENT_MODE) {
     for (int n = 0; n < N; ++n) {
       size_t b = 0;
@@ -1395,13 +1387,33 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
     }
   } else if (call == CPG_CALL_ALS || call == CPG_CALL_NTF) {
     const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
-    const size_t ypn = pitched_elems(lr.J, lr.K, is_f64(prec) ? 8 : 4);
+    const size_t ypn = with_copy ? pitched_elems(lr.J, lr.K, is_f64(prec) ? 8 : 4) : 0;
     if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes, ypn);
     else carve_als<float>(nullptr, s, R, lr, ll, &bytes, ypn);
   } else {
     return 0;
   }
   return bytes;
+}
+
+}  // namespace
+
+namespace cpg {
+size_t workspace_bytes_required(const int64_t* I, int N, int R, const cpg_opts* opts, int call) {
+  return workspace_size_impl(I, N, R, opts, call, false);
+}
+}  // namespace cpg
+
+extern "C" {
+
+int cpg_split_point(const int64_t* I, int N) {
+  Shape s;
+  if (check_shape(I, N, 1, s) != CPG_OK) return 0;
+  return split_point(s);
+}
+
+size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call) {
+  return workspace_size_impl(I, N, R, opts, call, true);
 }
 
 cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R, void* const* G,

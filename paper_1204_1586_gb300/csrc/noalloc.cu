@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/cpgrad.h"
+#include "api_internal.h"
 
 namespace {
 
@@ -46,7 +47,9 @@ extern "C" cpg_status cp_gradient_all_noalloc(const void* Y, const int64_t* I, i
   o.precision = precision;
   o.split = split;
   o.stream = stream;
-  const size_t need = cpg_workspace_size(I, N, R, &o, CPG_CALL_GRADIENT_ALL);
+  // The fixed array need not hold the optional pitched copy of Y: without
+  // room for it the gradient streams Y itself.
+  const size_t need = cpg::workspace_bytes_required(I, N, R, &o, CPG_CALL_GRADIENT_ALL);
   if (need == 0) return CPG_ERR_ARG;
   if (need > size_t(CPG_NOALLOC_WORKSPACE_BYTES)) return CPG_ERR_WORKSPACE;
   void* scratch = nullptr;

@@ -233,3 +233,22 @@ def test_selftest_timeout_arguments(L):
     assert L.cpg_selftest_timeout(ctypes.byref(_opts(ws=dummy, nbytes=256)), 0) == cpgrad.CPG_ERR_ARG
     assert L.cpg_selftest_timeout(ctypes.byref(_opts(ws=dummy, nbytes=256)), (1 << 24) + 1) == cpgrad.CPG_ERR_ARG
     assert cpgrad.launch_count() == 0 * n0
+
+
+def test_noalloc_bound_leaves_out_the_pitched_copy(L):
+    """The no-allocation entry point's fixed 64 MB scratch need not hold the
+    optional pitched copy of Y: a 17^6 tensor (column pitch 4913 floats at
+    the split k = 3) asks 96 MB more than that for the copy, yet its other
+    scratch fits, so the call passes the size check.  Without a GPU it then
+    fails at the device query with CPG_ERR_CUDA, launching nothing."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("dummy pointers: this check runs only where no GPU can be reached")
+    I = [17] * 6
+    assert cpgrad.cpg_workspace_size(I, 6) > (64 << 20)
+    I64 = (ctypes.c_int64 * 6)(*I)
+    dummy = ctypes.c_void_p(256)
+    P = (ctypes.c_void_p * 6)(*([dummy] * 6))
+    st = L.cp_gradient_all_noalloc(dummy, I64, 6, P, 6, P, 0, 0, None)
+    assert st != cpgrad.CPG_ERR_WORKSPACE
+    assert st == cpgrad.CPG_ERR_CUDA
