@@ -894,7 +894,9 @@ bool tuned_choice(const Shape& s, int R, const cpg_opts* o, GradChoice* c) {
 // workspace holds it, else the planner's.
 GradChoice grad_choice(const Shape& s, int R, const cpg_opts* o) {
   GradChoice c;
-  if (tuned_choice(s, R, o, &c) && o->workspace_bytes >= grad_bytes(s, R, o->precision, c)) return c;
+  // The measured plan whenever the workspace holds it, with or without room
+  // for the pitched copy of Y (the call takes the copy only when it fits).
+  if (tuned_choice(s, R, o, &c) && o->workspace_bytes >= grad_bytes(s, R, o->precision, c, false)) return c;
   return default_choice(s, R, o);
 }
 
