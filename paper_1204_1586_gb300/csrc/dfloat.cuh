@@ -63,16 +63,6 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
 // acc + a * b with a, b floats: the product is exact before the addition.
 __device__ __forceinline__ df df_add_prod_ff(df acc, float a, float b) { return df_add(acc, two_prod(a, b)); }
 
-__device__ __forceinline__ df df_div(df a, df b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  df r = df_sub(a, df_mul_f(b, q1));
-  const float q2 = __fdiv_rn(r.hi, b.hi);
-  r = df_sub(r, df_mul_f(b, q2));
-  const float q3 = __fdiv_rn(r.hi, b.hi);
-  df q = quick_two_sum(q1, q2);
-  return df_add(q, df_make(q3));
-}
-
 __device__ __forceinline__ df df_sqrt(df a) {
   if (a.hi <= 0.0f) return df{0.0f, 0.0f};
   const float s = __fsqrt_rn(a.hi);
