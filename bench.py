@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -120,7 +121,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"cpgrad_clocks_gpu{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -156,6 +157,10 @@ class ClockSampler:
                 for name, v in zip(names, parts[5:9]):
                     if v.lower() == "active":
                         reasons.add(name)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
