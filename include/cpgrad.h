@@ -67,13 +67,23 @@ typedef enum {
 
 /* Arithmetic of the leading contraction (Algorithm 2, steps 4 and 7), the
  * part that streams Y.  Everything after it runs in FP32 (FP64 for
- * CPG_FP64), and the CP_ALS normal equations always run in FP64. */
+ * CPG_FP64).  The CP_ALS normal equations run in double-float arithmetic
+ * (pairs of floats, about 48 significant bits) for FP32 data and in FP64 for
+ * CPG_FP64.  The split BF16 forms split each FP32 value into BF16 limbs
+ * (round to nearest) and keep the products of total limb order below the
+ * limb count (Henry, Tang and Heinecke, 2019); each tensor-core stage's
+ * partial sums are added into FP32 running sums with round-to-nearest adds.
+ * The iterative sweeps (cp_als_iter, cp_ntf_iter, cp_als_batched) accept
+ * CPG_FP32, CPG_TF32X3, CPG_BF16X6 and CPG_FP64 only (CPG_ERR_UNSUPPORTED
+ * otherwise): one and two BF16 limbs carry about 9 and 17 significant bits,
+ * an error each sweep's solve would carry into the factors. */
 typedef enum {
-  CPG_FP32 = 0,    /* FP32 CUDA-core FMA, FP32 accumulation                     */
-  CPG_TF32X3 = 1,  /* 3-term split TF32 products on tcgen05, FP32 accumulation */
-  CPG_BF16X3 = 2,  /* 3-term split BF16 products on tcgen05, FP32 accumulation */
-  CPG_BF16 = 3,    /* single BF16 product on tcgen05, FP32 accumulation        */
-  CPG_FP64 = 4     /* FP64 tensor and factors, FP64 CUDA-core FMA              */
+  CPG_FP32 = 0,    /* FP32 CUDA-core FMA, FP32 accumulation                        */
+  CPG_TF32X3 = 1,  /* 3-term split TF32 products on tcgen05, FP32 accumulation    */
+  CPG_BF16X3 = 2,  /* two BF16 limbs, 3 products on tcgen05 (gradient calls only) */
+  CPG_BF16 = 3,    /* one BF16 limb, 1 product on tcgen05 (gradient calls only)   */
+  CPG_FP64 = 4,    /* FP64 tensor and factors, FP64 CUDA-core FMA                 */
+  CPG_BF16X6 = 5   /* three BF16 limbs, 6 products on tcgen05                     */
 } cpg_precision;
 
 typedef struct {

@@ -8,4 +8,5 @@ from .cpgrad import (  # noqa: F401
     cpg_device_status, cp_gradient_autotune, gradient_plan, autotune_clear, cp_gradient_full, cp_gradient_step,
     cp_ntf_iter, selftest_timeout,
     colmajor, launch_count, profile_lead, profile_read, Workspace, CpgError, PRECISIONS, LAUNCH_KINDS, lib,
+    CPG_OK, CPG_ERR_ARG, CPG_ERR_WORKSPACE, CPG_ERR_UNSUPPORTED, CPG_ERR_TIMEOUT,
 )

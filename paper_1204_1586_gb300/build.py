@@ -21,7 +21,8 @@ LIB = os.path.join(PKG, "libcpgrad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
-SOURCES = ["lead_f32.cu", "lead_f64.cu", "lead_tc.cu", "lead_tf32.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["lead_f32.cu", "lead_f64.cu", "lead_tc.cu", "lead_ws1.cu", "lead_ws2.cu", "lead_ws3.cu", "lead_tf32.cu",
+           "api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libcpgrad.so")
 
 CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR_CUDA, CPG_ERR_TIMEOUT, \
     CPG_ERR_UNSUPPORTED = range(8)
-PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4}
+PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4, "bf16x6": 5}
 CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE, CALL_GRADIENT_FULL, CALL_NTF = 0, 1, 2, 3, 4, 5
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",

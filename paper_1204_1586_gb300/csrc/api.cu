@@ -17,8 +17,8 @@
 #include "lead_dispatch.cuh"
 #include "tensor_map.h"
 #include "api_internal.h"
-#include "lead_tc.cuh"
 #include "lead_tc_dispatch.cuh"
+#include "lead_ws.cuh"
 
 using namespace cpg;
 
@@ -130,11 +130,17 @@ int split_point(const Shape& s) {
 }
 
 bool is_f64(int prec) { return prec == CPG_FP64; }
+bool prec_valid(int prec) { return prec >= CPG_FP32 && prec <= CPG_BF16X6; }
+// Precisions of the iterative sweeps (CP_ALS, NTF, batched CP_ALS): those
+// whose gradient stays within 1e-5 of the exact one at every size.  BF16 (one
+// limb, about 2^-9) and BF16x3 (two limbs, about 2^-17 per element) are
+// gradient-only: each sweep's solve would carry their error into the factors.
+bool sweep_prec_ok(int prec) { return prec != CPG_BF16 && prec != CPG_BF16X3; }
 
 // ---- leading-pass plan ----------------------------------------------------------
 struct LeadPlan {
   bool tc = false;  // tensor-core kernel (split BF16 / TF32 products)
-  int tc_prec = 0;  // 0 = BF16x3, 1 = BF16, 2 = TF32x3
+  int tc_prec = 0;  // kTcBf16x3, kTcBf16, kTcTf32x3 or kTcBf16x6 (lead_tc_dispatch.cuh)
   int RTP = 0;      // tensor-core rank tile
   int k = 0, sides = 0;
   int64_t J = 0, K = 0;
@@ -153,7 +159,12 @@ SimtShape shape_for(int prec, int r, int sides) {
   return is_f64(prec) ? simt_shape_f64(r, sides) : simt_shape_f32(r, sides);
 }
 
-bool is_tc_prec(int prec) { return prec == CPG_BF16X3 || prec == CPG_BF16 || prec == CPG_TF32X3; }
+bool is_tc_prec(int prec) {
+  return prec == CPG_BF16X3 || prec == CPG_BF16 || prec == CPG_TF32X3 || prec == CPG_BF16X6;
+}
+int tc_code(int prec) {
+  return prec == CPG_BF16X3 ? kTcBf16x3 : prec == CPG_BF16 ? kTcBf16 : prec == CPG_TF32X3 ? kTcTf32x3 : kTcBf16x6;
+}
 
 // Grid over (J-blocks, K-splits): the K-split count that best fills `slots`
 // resident CTAs, discounting CTAs that run only a few stages.
@@ -230,7 +241,7 @@ void choose_grid(LeadPlan& p, int R, int esize, int slots) {
 LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   LeadPlan p;
   p.tc = true;
-  p.tc_prec = (prec == CPG_BF16X3) ? 0 : (prec == CPG_BF16) ? 1 : 2;
+  p.tc_prec = tc_code(prec);
   p.k = k;
   p.sides = sides;
   p.J = prod(s, 0, k);
@@ -242,12 +253,11 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   p.TK = tc_tile_cols(p.tc_prec, sides);
   const int64_t tiles = (p.J + p.TJ - 1) / p.TJ;
   if (sides == 2) {
-    // Step 7 alone: row tiles outer, one tensor-memory accumulator per column
-    // chunk (at most 512 / NW chunks per CTA), W_L built once per row tile.
-    // Minimise waves * (super-stages + W_L builds + fixed cost) + partial-sum
+    // Step 7 alone: row tiles outer, one tensor-memory running sum per column
+    // chunk (at most tc_max_acc chunks per CTA), W_L built once per row tile.
+    // Minimise waves * (stages + W_L builds + fixed cost) + partial-sum
     // traffic, as choose_grid does for the CUDA-core kernel (1 CTA per SM).
-    const int nw = p.tc_prec == 1 ? p.RTP : 2 * p.RTP;
-    const int64_t max_per = std::max(1, 512 / nw);
+    const int64_t max_per = std::max(1, tc_max_acc(p.RTP, 2, p.tc_prec));
     const int64_t chunks = (p.K + p.TK - 1) / p.TK;
     const int slots = num_sms();
     const double wbuild = 0.25 * p.RTP / 16.0;  // one W_L build, in super-stages
@@ -278,7 +288,7 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
     p.nKs = int((chunks + best_per - 1) / best_per);
     p.Kc = best_per * p.TK;
   } else {
-    const int cap = std::min(tc_max_nrt(p.RTP, sides, p.tc_prec), 8);
+    const int cap = sides == 3 ? tc_fused_max_nrt(p.RTP, p.tc_prec) : std::min(tc_max_acc(p.RTP, 1, p.tc_prec), 8);
     p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
     p.nJb = int((p.J + int64_t(p.TJ) * p.nrt - 1) / (int64_t(p.TJ) * p.nrt));
     choose_ksplit(p, num_sms());
@@ -440,7 +450,7 @@ GradWs<T> carve_grad(void* base, const Shape& s, int R, const LeadPlan& lp, size
 // 100^4, R = 10 the fused pass ran at 2.0 TB/s against 5.1 and 4.2 TB/s for
 // the single sides).
 bool use_fused(const Shape& s, int R, int k, int prec) {
-  if (prec == CPG_TF32X3) return false;  // the split-TF32 kernel runs one side per pass
+  if (is_tc_prec(prec) && !tc_fused_ok(tc_rank_tile(std::min(R, 64)), tc_code(prec))) return false;
   if (!is_tc_prec(prec) && R > 4) return false;
   const LeadPlan f = plan_lead(s, R, k, 3, prec);
   return double(f.lpart_elems + f.rpart_elems) <= 0.2 * double(s.total);
@@ -799,7 +809,7 @@ cpg_status common_checks(const cpg_opts* opts, Shape& s, const int64_t* I, int N
   if (opts == nullptr) return CPG_ERR_ARG;
   cpg_status st = check_shape(I, N, R, s);
   if (st != CPG_OK) return st;
-  if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
+  if (!prec_valid(opts->precision)) return CPG_ERR_ARG;
   if (opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return CPG_ERR_ARG;
   return CPG_OK;
 }
@@ -858,7 +868,7 @@ std::vector<GradChoice> grad_candidates(const Shape& s, int R, const cpg_opts* o
     c.k = k;
     c.fused = false;
     v.push_back(c);
-    if (prec != CPG_TF32X3) {
+    if (!is_tc_prec(prec) || tc_fused_ok(tc_rank_tile(std::min(R, 64)), tc_code(prec))) {
       const LeadPlan f = plan_lead(s, R, k, 3, prec);
       if (double(f.lpart_elems + f.rpart_elems) <= double(s.total)) {
         c.fused = true;
@@ -1361,7 +1371,7 @@ size_t workspace_size_impl(const int64_t* I, int N, int R, const cpg_opts* opts,
   Shape s;
   if (check_shape(I, N, R, s) != CPG_OK) return 0;
   const int prec = opts ? opts->precision : CPG_FP32;
-  if (prec < CPG_FP32 || prec > CPG_FP64) return 0;
+  if (!prec_valid(prec)) return 0;
   if (opts && opts->split != 0 && (opts->split < 1 || opts->split > N - 1)) return 0;
   const int k = choose_split(s, opts);
   size_t bytes = 0;
@@ -1522,6 +1532,7 @@ cpg_status cp_als_iter(const void* Y, const int64_t* I, int N, void* const* A, d
   if (st != CPG_OK) return st;
   if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || lambda == nullptr || iters < 0)
     return CPG_ERR_ARG;
+  if (!sweep_prec_ok(opts->precision)) return CPG_ERR_UNSUPPORTED;
   if (iters == 0) return CPG_OK;
   if (is_f64(opts->precision)) return als_impl<double>(s, static_cast<const double*>(Y), A, lambda, R, iters, fit, opts);
   return als_impl<float>(s, static_cast<const float*>(Y), A, lambda, R, iters, fit, opts);
@@ -1559,6 +1570,7 @@ cpg_status cp_ntf_iter(const void* Y, const int64_t* I, int N, void* const* A, i
   cpg_status st = common_checks(opts, s, I, N, R);
   if (st != CPG_OK) return st;
   if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || iters < 0) return CPG_ERR_ARG;
+  if (!sweep_prec_ok(opts->precision)) return CPG_ERR_UNSUPPORTED;
   if (iters == 0) return CPG_OK;
   if (is_f64(opts->precision))
     return als_impl<double>(s, static_cast<const double*>(Y), A, nullptr, R, iters, fit, opts, nullptr, true);
@@ -1645,7 +1657,8 @@ size_t cpg_workspace_size_batched(int B, const cpg_tensor_desc* descs, const cpg
 
 cpg_status cp_als_batched(int B, const cpg_tensor_desc* descs, int iters, const cpg_opts* opts) {
   if (opts == nullptr || B < 1 || descs == nullptr || iters < 0) return CPG_ERR_ARG;
-  if (opts->precision < CPG_FP32 || opts->precision > CPG_FP64) return CPG_ERR_ARG;
+  if (!prec_valid(opts->precision)) return CPG_ERR_ARG;
+  if (!sweep_prec_ok(opts->precision)) return CPG_ERR_UNSUPPORTED;
   // Validate every member before launching anything.
   std::vector<Shape> shapes(B);
   std::vector<size_t> off(B);

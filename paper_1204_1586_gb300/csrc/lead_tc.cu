@@ -1,66 +1,83 @@
-// Host side of the tensor-core leading contraction: TMA tensor map of Y and
-// the kernel instances (rank tile 16 / 32 / 64, sides, BF16x3 or BF16); the
-// split-TF32 form is forwarded to lead_tf32.cu.
-#include "lead_tc.cuh"
+// Host side of the tensor-core leading contractions: the TMA tensor map of Y
+// for the split-BF16 kernel (lead_ws.cuh), instance dispatch, and the plan
+// limits the planner reads.  The split-TF32 form is forwarded to lead_tf32.cu.
 #include "lead_tc_dispatch.cuh"
-#include "tensor_map.h"
+#include "lead_tf32.cuh"
+#include "lead_ws_host.cuh"
 
 namespace cpg {
 
 namespace {
 
-// Y as a 2-D tensor [K][J] (J contiguous); one box = 128 rows x 64 columns.
-bool make_y_map(CUtensorMap* m, const float* Y, int64_t J, int64_t K, int64_t ldy) {
-  return make_matrix_map(m, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, J, K, 128, 64, CU_TENSOR_MAP_SWIZZLE_NONE, ldy);
-}
+int limbs_of(int prec) { return prec == kTcBf16 ? 1 : prec == kTcBf16x6 ? 3 : 2; }
 
-template <int RTP, int SIDES, int PREC>
-cudaError_t run(const CUtensorMap& m, const TcArgs& a, dim3 grid, cudaStream_t st) {
-  using C = TcCfg<RTP, SIDES, PREC>;
-  auto kern = lead_tc_kernel<RTP, SIDES, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::smem_bytes));
-  if (e != cudaSuccess) return e;
-  return launch_pdl(kern, grid, dim3(C::NT), C::smem_bytes, st, m, a);
-}
-
-template <int RTP, int PREC>
-cudaError_t run_sides(const CUtensorMap& m, const TcArgs& a, int sides, dim3 grid, cudaStream_t st) {
-  switch (sides) {
-    case 1: return run<RTP, 1, PREC>(m, a, grid, st);
-    case 2: return run<RTP, 2, PREC>(m, a, grid, st);
-    case 3: return run<RTP, 3, PREC>(m, a, grid, st);
-    default: return cudaErrorInvalidValue;
+template <int SIDES, int L>
+int ws_max_acc_rtp(int RTP) {
+  switch (RTP) {
+    case 16: return WsCfg<16, SIDES, L>::MAX_ACC;
+    case 32: return WsCfg<32, SIDES, L>::MAX_ACC;
+    default:
+      if constexpr (SIDES != 3) return WsCfg<64, SIDES, L>::MAX_ACC;
+      return 0;
   }
 }
 
-template <int RTP>
-cudaError_t run_prec(const CUtensorMap& m, const TcArgs& a, int sides, int prec, dim3 grid, cudaStream_t st) {
-  return prec == 0 ? run_sides<RTP, 0>(m, a, sides, grid, st) : run_sides<RTP, 1>(m, a, sides, grid, st);
+template <int SIDES>
+int ws_max_acc(int RTP, int L) {
+  if (L == 1) return ws_max_acc_rtp<SIDES, 1>(RTP);
+  if (L == 2) return ws_max_acc_rtp<SIDES, 2>(RTP);
+  if constexpr (SIDES != 3) return ws_max_acc_rtp<SIDES, 3>(RTP);
+  return 0;
 }
 
 }  // namespace
 
 int tc_rank_tile(int r) { return r <= 16 ? 16 : r <= 32 ? 32 : 64; }
 
-int tc_max_nrt(int RTP, int sides, int prec) {
-  const int nw = (prec == 1) ? RTP : 2 * RTP;
-  if (sides == 2) return 1 << 20;     // row tiles are outer: any number per CTA
-  return sides == 1 ? 512 / nw : 512 / nw - 2;  // fused: two step-7 accumulators
+int tc_tile_rows(int prec, int sides) {
+  if (prec == kTcTf32x3) return sides == 1 ? 128 : 64;
+  return sides == 2 ? 64 : 128;
+}
+int tc_tile_cols(int prec, int sides) {
+  if (prec == kTcTf32x3) return sides == 1 ? 64 : 128;
+  return sides == 1 ? 64 : 128;
 }
 
-int tc_tile_rows(int prec, int sides) { return prec == 2 ? (sides == 1 ? 128 : 64) : 128; }
-int tc_tile_cols(int prec, int sides) { return prec == 2 ? (sides == 1 ? 64 : 128) : 128; }
+int tc_max_acc(int RTP, int sides, int prec) {
+  if (prec == kTcTf32x3) return 512 / (2 * RTP);
+  const int L = limbs_of(prec);
+  switch (sides) {
+    case 1: return ws_max_acc<1>(RTP, L);
+    case 2: return ws_max_acc<2>(RTP, L);
+    case 3: return ws_max_acc<3>(RTP, L);
+    default: return 0;
+  }
+}
+
+bool tc_fused_ok(int RTP, int prec) { return prec != kTcTf32x3 && limbs_of(prec) <= 2 && RTP <= 32; }
+
+int tc_fused_max_nrt(int RTP, int prec) {
+  if (!tc_fused_ok(RTP, prec)) return 0;
+  const int nwlc = RTP <= 16 ? WsCfg<16, 3, 1>::NWLC : WsCfg<32, 3, 1>::NWLC;
+  return std::min(nwlc, tc_max_acc(RTP, 3, prec) - 1);
+}
 
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {
-  if (prec == 2) return launch_lead_tf32(Y, a, RTP, sides, grid, st);
+  if (prec == kTcTf32x3) return launch_lead_tf32(Y, a, RTP, sides, grid, st);
   CUtensorMap m{};
   TcArgs b = a;
   b.Y = Y;
-  b.use_tma = make_y_map(&m, Y, a.J, a.K, a.ldy) ? 1 : 0;  // else element copies (rows not 16-byte aligned)
-  switch (RTP) {
-    case 16: return run_prec<16>(m, b, sides, prec, grid, st);
-    case 32: return run_prec<32>(m, b, sides, prec, grid, st);
-    case 64: return run_prec<64>(m, b, sides, prec, grid, st);
+  // One box = 32 KB: 128 rows x 64 columns (steps 4 and fused), 64 x 128 (step 7).
+  const uint32_t ru = sides == 2 ? 64 : 128, cu = 8192 / ru;
+  b.use_tma = make_matrix_map(&m, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.J, a.K, ru, cu, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              a.ldy)
+                  ? 1
+                  : 0;
+  const int L = limbs_of(prec);
+  switch (sides) {
+    case 1: return launch_ws_sides1(m, b, RTP, L, grid, st);
+    case 2: return launch_ws_sides2(m, b, RTP, L, grid, st);
+    case 3: return launch_ws_sides3(m, b, RTP, L, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,4 +1,4 @@
-// Host-side entry points of the tensor-core leading contraction.
+// Host-side entry points of the tensor-core leading contractions.
 #pragma once
 
 #include "common.cuh"
@@ -7,21 +7,29 @@ namespace cpg {
 
 struct TcArgs;
 
+// Tensor-core precision codes of a leading pass: 0 = BF16x3 (two BF16 limbs),
+// 1 = BF16 (one limb), 2 = TF32x3 (split TF32, lead_tf32.cu), 3 = BF16x6
+// (three BF16 limbs).
+constexpr int kTcBf16x3 = 0, kTcBf16 = 1, kTcTf32x3 = 2, kTcBf16x6 = 3;
+
 // Rank tile (MMA N of one product) for r rank columns: 16, 32 or 64.
 int tc_rank_tile(int r);
-// Largest number of 128-row tiles per J-block the fused kernel can keep in
-// tensor memory (no limit for a single side).
-int tc_max_nrt(int RTP, int sides, int prec);
-// TMA needs a 16-byte aligned tensor and rows of whole 16-byte chunks.
-// prec: 0 = BF16x3 split product, 1 = single BF16 product, 2 = TF32x3 split
-// product (one side per pass: sides 1 or 2).
-cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st);
-// The split-TF32 kernel (lead_tf32.cu): rows tiles of 128 x 64 (step 4) or
-// 64 x 128 (step 7).
-cudaError_t launch_lead_tf32(const float* Y, const TcArgs& a, int RTP, int sides, dim3 grid, cudaStream_t st);
-// Row and column extent of one super-stage of the tensor-core kernel for
-// (prec, sides).
+// Rows and columns of one stage for (prec, sides).
 int tc_tile_rows(int prec, int sides);
 int tc_tile_cols(int prec, int sides);
+// Largest number of running sums a CTA keeps in tensor memory: row tiles of a
+// J-block (step 4, and the fused pass, which needs one more for step 7) or
+// column chunks (step 7).
+int tc_max_acc(int RTP, int sides, int prec);
+// Whether one pass can compute steps 4 and 7 for (RTP, prec), and how many row
+// tiles per J-block it can keep the step-7 Khatri-Rao tiles of.
+bool tc_fused_ok(int RTP, int prec);
+int tc_fused_max_nrt(int RTP, int prec);
+// TMA needs a 16-byte aligned tensor and rows of whole 16-byte chunks; other
+// tensors are read with element loads.
+cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st);
+// The split-TF32 kernel (lead_tf32.cu): row tiles of 128 x 64 (step 4) or
+// 64 x 128 (step 7), one side per pass.
+cudaError_t launch_lead_tf32(const float* Y, const TcArgs& a, int RTP, int sides, dim3 grid, cudaStream_t st);
 
 }  // namespace cpg

@@ -42,7 +42,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
-#include "lead_tc.cuh"
+#include "lead_ws.cuh"
 #include "tc_common.cuh"
 
 namespace cpg {

@@ -1,9 +1,10 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances: relative Frobenius error per mode <= 1e-5 for the FP32 path and
-the split BF16x3 / TF32x3 products, 2e-2 for pure BF16, and <= 1e-12 for the
-FP64 path (the bounds the method's target states for FP32
-and a choice for FP64).  ALS fits agree within 1e-5 (FP32) / 1e-9 (FP64)."""
+the split BF16x3 / BF16x6 / TF32x3 products, 2e-2 for pure BF16, and
+<= 1e-12 for the FP64 path (the bounds the method's target states for FP32
+and a choice for FP64).  CP_ALS (FP32, TF32x3, BF16x6): fits within 1e-5,
+factors and lambda after a sweep within 1e-5 relative; FP64 within 1e-9."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5, "bf16": 2e-2}
+TOL = {"fp32": 1e-5, "fp64": 1e-12, "bf16x3": 1e-5, "bf16x6": 1e-5, "tf32x3": 1e-5, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -77,6 +78,15 @@ GRAD_CASES = [
     ([20, 12, 40, 36], 33, "bf16x3"),   # rank tile 64, R not a multiple of 16
     ([40, 36, 28, 20], 16, "bf16"),
     ([100, 100, 100], 10, "bf16"),
+    # three BF16 limbs (six products)
+    ([24, 20, 30, 17], 12, "bf16x6"),   # k=2, J=480: ragged row tile and column chunk
+    ([100, 100, 100], 20, "bf16x6"),    # k=1, J=100, rank tile 32
+    ([64, 64, 64, 4], 3, "bf16x6"),     # K=16384: many column chunks per CTA
+    ([32, 16, 20, 24, 10], 10, "bf16x6"),
+    ([12, 11, 10, 9], 64, "bf16x6"),    # rank tile 64
+    ([9, 10, 11], 70, "bf16x6"),        # J=9: element loads, two rank groups
+    ([15, 15, 15, 15, 15], 10, "bf16x6"),  # J=225: element loads
+    ([20, 12, 40, 36], 33, "bf16x6"),   # rank tile 64, R not a multiple of 16
     # split-TF32 products on the tensor cores (one side per pass; 128 x 64
     # step-4 tiles, 64 x 128 step-7 tiles)
     ([24, 20, 30, 17], 12, "tf32x3"),   # k=2, J=480: TMA boxes, ragged row tile and column chunk
@@ -118,6 +128,7 @@ def test_gradient_all_split_override(cg, split):
                                       ([200, 3, 4], 6, "fp32"), ([3, 4, 200], 6, "fp32"),
                                       ([13, 7, 9, 11], 8, "fp64"), ([40, 12, 8, 20], 8, "bf16x3"),
                                       ([4, 8, 300], 6, "bf16x3"), ([40, 12, 8, 20], 8, "tf32x3"),
+                                      ([40, 12, 8, 20], 8, "bf16x6"), ([4, 8, 300], 6, "bf16x6"),
                                       ([4, 8, 300], 6, "tf32x3")])
 def test_gradient_mode(cg, I, R, prec):
     y, A, dt = inputs(I, R, prec, seed=5)
@@ -156,7 +167,7 @@ def test_gradient_deterministic(cg):
 
 
 @pytest.mark.parametrize("R", [10, 20])
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16"])
 def test_precision_study_7d(cg, R, prec):
     """The 7-D collinear workload's recipe (factor columns with pairwise
     cosine 0.5, 30 dB noise) at I = 7 per mode: per-mode relative Frobenius
@@ -171,10 +182,14 @@ def test_precision_study_7d(cg, R, prec):
     want = oracle.cp_gradient_all(p.y.astype(np.float64), p.I, p.factors)
     errs = [rel(G[n].double().cpu().numpy(), want[n]) for n in range(7)]
     assert max(errs) <= TOL[prec], errs
+    if prec == "bf16":
+        # One BF16 limb carries 8 significant bits: an error at FP32 level
+        # would mean the call did not run the BF16 products.
+        assert min(errs) > 1e-4, errs
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6", "tf32x3"])
 def test_gradient_full_size_sampled(cg, prec):
     """The 4-D 100^4, R = 10 workload in the benchmark's launch configuration;
     sampled entries g_r^(n)[i] checked one by one with the oracle (eq. 3.2)."""
@@ -194,6 +209,8 @@ def test_gradient_full_size_sampled(cg, prec):
             i, r = int(rng.integers(I[n])), int(rng.integers(R))
             w = oracle.cp_gradient_entry(p.y, I, p.init, n, i, r)
             assert abs(want[n][i, r] - w) <= 1e-9 * max(1.0, abs(w))
+    if prec == "bf16x3":
+        return  # gradient-only precision
     # one ALS sweep from the same start: fit against the oracle's fit
     Ad = [dev_factor(a, np.float32) for a in p.init]
     lam, fit = cg.cp_als_iter(Y, I, Ad, 1, precision=prec)
@@ -204,7 +221,7 @@ def test_gradient_full_size_sampled(cg, prec):
 
 @pytest.mark.parametrize("I,R,prec,iters", [([30, 40, 50], 5, "fp64", 10), ([24, 20, 30, 17], 6, "fp32", 6),
                                             ([12, 10, 8, 9, 7], 4, "fp32", 5), ([40, 30], 3, "fp32", 8),
-                                            ([24, 20, 30, 17], 6, "bf16x3", 6), ([40, 36, 28], 5, "bf16x3", 5),
+                                            ([24, 20, 30, 17], 6, "bf16x6", 6), ([40, 36, 28], 5, "bf16x6", 5),
                                             ([24, 20, 30, 17], 6, "tf32x3", 6), ([40, 36, 28], 5, "tf32x3", 5)])
 def test_als_matches_oracle(cg, I, R, prec, iters):
     dt = np.float64 if prec == "fp64" else np.float32
@@ -214,9 +231,7 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     lam, fit = cg.cp_als_iter(Y, I, Ad, iters, precision=prec)
     torch.cuda.synchronize()
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=iters)
-    # Gauss-Seidel sweeps feed each gradient's error into the next factors, so
-    # the split product's ~1e-6 gradient error grows along the trajectory.
-    ftol = {"fp64": 1e-9, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-4}[prec]
+    ftol = 1e-9 if prec == "fp64" else 1e-5
     np.testing.assert_allclose(fit.cpu().numpy(), tr.fits, atol=ftol)
     if prec == "fp64":
         for n in range(len(I)):
@@ -225,7 +240,7 @@ def test_als_matches_oracle(cg, I, R, prec, iters):
     assert cg.cpg_device_status() == 0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x6"])
 def test_als_one_sweep_factors(cg, prec):
     """Per-sweep parity from identical factors."""
     I, R = [24, 20, 30, 17], 6
@@ -234,10 +249,7 @@ def test_als_one_sweep_factors(cg, prec):
     lam, fit = cg.cp_als_iter(torch.from_numpy(p.y).cuda(), I, Ad, 1, precision=prec)
     torch.cuda.synchronize()
     tr = oracle.cp_als(p.y.astype(np.float64), I, p.init, iters=1)
-    # A = G V^{-1} (eq. 2.14): the solve amplifies the gradient's error by the
-    # conditioning of V, so the BF16x3 split product (gradient error ~6e-6)
-    # gets 5e-5 for the factors and for lambda (the norms of G V^{-1}).
-    tol = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 5e-5}[prec]
+    tol = 1e-5
     for n in range(len(I)):
         assert rel(Ad[n].double().cpu().numpy(), tr.A[n]) <= tol, n
     np.testing.assert_allclose(lam.cpu().numpy(), tr.lam, rtol=tol)
@@ -272,3 +284,15 @@ def test_als_singular_status(cg):
     assert cg.cpg_device_status() == 4
     assert torch.equal(Ad[0], before)
     assert cg.cpg_device_status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_sweeps_refuse_gradient_only_precisions(cg, prec):
+    """One or two BF16 limbs are gradient-only: CP_ALS returns
+    CPG_ERR_UNSUPPORTED before launching anything."""
+    I, R = [12, 10, 8], 3
+    p = cpsynth.make_problem(I, R, snr_db=20.0, seed=14, dtype=np.float32)
+    Ad = [dev_factor(a, np.float32) for a in p.init]
+    with pytest.raises(cg.CpgError) as e:
+        cg.cp_als_iter(torch.from_numpy(p.y).cuda(), I, Ad, 1, precision=prec)
+    assert e.value.status == cg.CPG_ERR_UNSUPPORTED
