@@ -18,6 +18,12 @@ launch overlap of consecutive kernels, so they stay out of the step timing).
 --impl reference times the FP64 CPU oracle (explicit unfoldings and
 Khatri-Rao products, Algorithm 1 + eq. 2.14) on the same workload, a bounded
 sample per step (one all-mode gradient and one ALS sweep).
+
+After the headline, "configs" measures every workload of the list (3-D FP64
+30x40x50, 100^4 R=10, 15^7 R=10/20 with collinear factors, 60^5 R=32/64,
+and the 256-member batch) at every precision that applies: gradient and
+CP_ALS sweep times, the leading passes' GB/s and roofline fractions, the
+error against the FP64 oracle, and the SM clocks seen (--no-configs skips it).
 """
 from __future__ import annotations
 
@@ -202,7 +208,8 @@ def cpu_baseline(p, budget_s=10.0):
         times.append(oracle_sample(p))
     dt = sum(times) / len(times)
     flops = gradient_flops(p.I, p.R) + als_sweep_flops(p.I, p.R)
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": openblas_threads(), "kind": "oracle",
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": openblas_threads(), "nproc": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"{len(times)} x (one all-mode gradient + one ALS sweep) of the FP64 oracle on the full "
                       f"{p.I} R={p.R} tensor, {sum(times):.1f} s in all, {dt:.2f} s each; flops counted as for "
                       f"the GPU step"}
@@ -226,7 +233,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "4-D FP32 tensor 100x100x100x100 (rank-10 CP model + 20 dB noise), R=10, "
                                    "oracle step = one all-mode gradient + one ALS sweep", "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "nproc": os.cpu_count(), "kind": "oracle",
                              "sample": "each step: one all-mode gradient (Algorithm 1 per mode) + one ALS sweep, "
                                        "full tensor"},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -243,13 +250,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16"],
                     help="arithmetic of the leading contraction (Algorithm 2 steps 4/7)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run for ncu: warm-up and timed steps only, no e2e, checks or CPU baseline")
     ap.add_argument("--workload", default="cp4d", choices=["cp4d", "batched"],
                     help="cp4d: the 4-D 100^4 R=10 step (default); batched: many independent tensors per call")
     ap.add_argument("--batch-count", type=int, default=256, help="members of the batched workload")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-config measurements (every workload and precision) after the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -389,7 +398,7 @@ def main():
     avg = sum(lead_ms) / len(lead_ms) if lead_ms else float("nan")
     achieved = ybytes / (avg / 1e3) / 1e9
     # The split forms run the tensor-core kernels (J = 10^4 rows are whole 16-byte chunks).
-    kernel = {"fp32": "lead_simt_kernel", "tf32x3": "lead_tf32_kernel"}.get(prec, "lead_tc_kernel")
+    kernel = {"fp32": "lead_simt_kernel", "tf32x3": "lead_tf32_kernel"}.get(prec, "lead_ws_kernel")
     traffic = lead_traffic(kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": f"{kernel} (Algorithm 2 steps 4/7)",
@@ -469,6 +478,12 @@ def main():
     del Yabs
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
+    if not args.no_configs:
+        del Ast
+        try:
+            line["configs"] = measure_configs(cg, dev, stream, hbm, args.batch_count)
+        except Exception as ex:  # keep the headline line whatever happens here
+            line["configs"] = {"error": f"{type(ex).__name__}: {str(ex)[:300]}"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -478,9 +493,199 @@ def main():
 LEAD_KERNELS = {
     # kernel family -> (sources whose hash identifies the captured build, traffic summary)
     "lead_simt_kernel": (("lead_simt.cuh", "common.cuh", "tc_common.cuh"), "lead_simt_traffic.json"),
-    "lead_tc_kernel": (("lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tc_traffic.json"),
-    "lead_tf32_kernel": (("lead_tf32.cuh", "lead_tc.cuh", "tc_common.cuh", "common.cuh"), "lead_tf32_traffic.json"),
+    "lead_ws_kernel": (("lead_ws.cuh", "tc_common.cuh", "common.cuh"), "lead_ws_traffic.json"),
+    "lead_tf32_kernel": (("lead_tf32.cuh", "lead_ws.cuh", "tc_common.cuh", "common.cuh"), "lead_tf32_traffic.json"),
 }
+
+
+# ---- every config of the workload list, every precision (informational keys) -----------
+SWEEP_PRECS = ("fp32", "tf32x3", "bf16x6")      # CP_ALS precisions
+GRAD_ONLY_PRECS = ("bf16x3", "bf16")            # gradient-only precisions
+
+
+def _rel_err_max(G, want):
+    return max(float(np.linalg.norm(G[n].double().cpu().numpy() - want[n]) / np.linalg.norm(want[n]))
+               for n in range(len(want)))
+
+
+def _measure_case(cg, Y, I, A0, G, ws, stream, prec, hbm, esize=4):
+    """Gradient (autotuned plan) and CP_ALS sweep times of one tensor at one
+    precision, the leading passes' GB/s (event-timed launch by launch), and
+    the fractions of the one-pass (gradient) and two-pass (sweep) floors."""
+    ybytes = esize * prod(I)
+    out = {}
+    plan = cg.cp_gradient_autotune(Y, I, A0, G, precision=prec, workspace=ws, reps=2)
+    out["gradient_plan"] = {"split": plan["split"], "fused": plan["fused"]}
+    tg = _time_component(lambda: cg.cp_gradient_all(Y, I, A0, G, workspace=ws, precision=prec), stream)
+    out["gradient_ms"] = tg
+    out["gradient_frac_of_one_pass_roofline"] = (ybytes / hbm / 1e6) / tg
+    cg.profile_lead(1)
+    cg.cp_gradient_all(Y, I, A0, G, workspace=ws, precision=prec)
+    passes = {}
+    if prec not in GRAD_ONLY_PRECS:
+        ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 5, workspace=ws, precision=prec),
+                             stream) / 5
+        out["als_sweep_ms"] = ta
+        out["als_frac_of_two_pass_roofline"] = (2 * ybytes / hbm / 1e6) / ta
+        cg.profile_lead(1)
+        cg.cp_als_iter(Y, I, [a.clone() for a in A0], 3, workspace=ws, precision=prec)
+    import torch
+    torch.cuda.synchronize()
+    for t, k in cg.profile_read():
+        name = {1: "step4_R", 2: "step7_L", 3: "step4+7_fused"}.get(k)
+        if name:
+            passes.setdefault(name, []).append(t)
+    cg.profile_lead(False)
+    out["pass_GBps"] = {k: ybytes / (statistics.median(v) / 1e3) / 1e9 for k, v in passes.items()}
+    out["pass_frac"] = {k: v / hbm for k, v in out["pass_GBps"].items()}
+    return out
+
+
+def measure_configs(cg, dev, stream, hbm, batch_count):
+    """Every config of the workload list (the 3-D FP64 correctness case, 100^4
+    R=10, 15^7 R=10/20, 60^5 R=32/64, the 256-member batch), each at every
+    precision that applies, with its error against the FP64 oracle (every
+    entry, or 100 sampled entries of eq. 3.2 at 60^5) and the SM clocks seen
+    while it ran.  Informational: the headline value stays the 100^4 step."""
+    import torch
+    import oracle
+    res = {}
+    ws = cg.Workspace(dev)
+
+    def colmaj(a):
+        return cg.colmajor(torch.from_numpy(np.asarray(a, dtype=np.float32)).to(dev))
+
+    def run_config(name, fn):
+        clk = ClockSampler(dev.index or 0)
+        clk.start()
+        t0 = time.time()
+        try:
+            r = fn()
+        except Exception as ex:
+            r = {"error": f"{type(ex).__name__}: {str(ex)[:200]}"}
+        r["clocks"] = clk.stop()
+        r["wall_s"] = round(time.time() - t0, 1)
+        res[name] = r
+
+    # 3-D FP64 30x40x50, R=5: latency-bound correctness case (times in us)
+    def c3d():
+        p = cpsynth.workload("cp3d_30x40x50_r5_fp64")
+        Y = torch.from_numpy(p.y).to(dev)
+        A0 = [cg.colmajor(torch.from_numpy(a).to(dev)) for a in p.init]
+        G = [torch.empty((p.R, In), dtype=torch.float64, device=dev).t() for In in p.I]
+        cg.cp_gradient_all(Y, p.I, A0, G, workspace=ws, precision="fp64")
+        want = oracle.cp_gradient_all(p.y, p.I, p.init)
+        err = _rel_err_max(G, want)
+        tg = _time_component(lambda: cg.cp_gradient_all(Y, p.I, A0, G, workspace=ws, precision="fp64"), stream)
+        A = [a.clone() for a in A0]
+        _, fit = cg.cp_als_iter(Y, p.I, A, 10, workspace=ws, precision="fp64")
+        tr = oracle.cp_als(p.y, p.I, p.init, iters=10)
+        ta = _time_component(lambda: cg.cp_als_iter(Y, p.I, [a.clone() for a in A0], 10, workspace=ws,
+                                                    precision="fp64"), stream) / 10
+        return {"precision": "fp64", "gradient_us": 1e3 * tg, "als_sweep_us": 1e3 * ta,
+                "gradient_rel_err_max": err,
+                "als_fit_abs_err_10_sweeps": float(np.max(np.abs(fit.cpu().numpy() - np.array(tr.fits))))}
+    run_config("cp3d_30x40x50_r5_fp64", c3d)
+
+    # 100^4 R=10 and 15^7 R=10/20: every precision, every entry against the oracle
+    for wname in ("cp4d_100_r10_fp32", "cp7d_15_r10_fp32", "cp7d_15_r20_fp32"):
+        def cfull(wname=wname):
+            p = cpsynth.workload(wname)
+            Y = torch.from_numpy(p.y).to(dev)
+            A0 = [colmaj(a) for a in p.init]
+            G = [torch.empty((p.R, In), dtype=torch.float32, device=dev).t() for In in p.I]
+            want = oracle.cp_gradient_all(p.y, p.I, [a.astype(np.float32).astype(np.float64) for a in p.init])
+            out = {}
+            for prec in SWEEP_PRECS + GRAD_ONLY_PRECS:
+                r = _measure_case(cg, Y, p.I, A0, G, ws, stream, prec, hbm)
+                cg.cp_gradient_all(Y, p.I, A0, G, workspace=ws, precision=prec)
+                r["gradient_rel_err_max"] = _rel_err_max(G, want)
+                out[prec] = r
+            return out
+        run_config(wname.replace("_fp32", ""), cfull)
+
+    # 60^5 R=32/64: one N(0,1) tensor; errors from 100 sampled entries (eq. 3.2)
+    I5 = [60] * 5
+    y5 = cpsynth.random_tensor(I5, seed=cpsynth.DEFAULT_SEED + 50)
+    Y5 = torch.from_numpy(y5).to(dev)
+    for R in (32, 64):
+        def c5d(R=R):
+            A = cpsynth.random_factors(I5, R, seed=cpsynth.DEFAULT_SEED + R)
+            A0 = [colmaj(a) for a in A]
+            G = [torch.empty((R, In), dtype=torch.float32, device=dev).t() for In in I5]
+            rng = np.random.default_rng(R)
+            samples = []
+            for n in range(5):
+                pairs = sorted((int(rng.integers(60)), int(rng.integers(R))) for _ in range(20))
+                samples.append((pairs, oracle.cp_gradient_entries(y5, I5, A, n, pairs)))
+            out = {}
+            for prec in SWEEP_PRECS + GRAD_ONLY_PRECS:
+                r = _measure_case(cg, Y5, I5, A0, G, ws, stream, prec, hbm)
+                cg.cp_gradient_all(Y5, I5, A0, G, workspace=ws, precision=prec)
+                errs = []
+                for n, (pairs, ref) in enumerate(samples):
+                    Gn = G[n].double().cpu().numpy()
+                    got = np.array([Gn[i, r_] for i, r_ in pairs])
+                    errs.append(float(np.sqrt(np.mean((got - ref) ** 2) / np.mean(np.square(ref)))))
+                r["gradient_rel_err_sampled"] = max(errs)
+                out[prec] = r
+            return out
+        run_config(f"cp5d_60_r{R}", c5d)
+    del Y5, y5
+    torch.cuda.empty_cache()
+
+    # the 256-member batch: 30 sweeps per member per call; three ways of running it
+    def cbatch():
+        shapes = cpsynth.batched_shapes(batch_count)
+        gen = torch.Generator(device=dev)
+        Ys, members, A0s, As = [], [], [], []
+        for b, (I, R) in enumerate(shapes):
+            gen.manual_seed(cpsynth.DEFAULT_SEED + 1 + b)
+            Ys.append(torch.randn(prod(I), generator=gen, device=dev))
+            A0 = [colmaj(a) for a in cpsynth.gaussian_factors(I, R, seed=cpsynth.DEFAULT_SEED + 1 + b, stream=1)]
+            A0s.append(A0)
+            As.append([a.clone() for a in A0])
+        entries = sum(prod(I) for I, _ in shapes)
+        lams = [torch.ones(R, dtype=torch.float64, device=dev) for _, R in shapes]
+        fits = [torch.zeros(BATCH_ITERS, dtype=torch.float64, device=dev) for _ in shapes]
+        members = [(Y, I, A, lam, fit) for Y, (I, _), A, lam, fit in zip(Ys, shapes, As, lams, fits)]
+
+        def reset():
+            for A, A0 in zip(As, A0s):
+                for a, a0 in zip(A, A0):
+                    a.copy_(a0)
+
+        def batched():
+            reset()
+            cg.cp_als_batched(members, BATCH_ITERS, workspace=ws)
+
+        def serial():
+            reset()
+            for Y, I, A, lam, fit in members:
+                cg.cp_als_iter(Y, I, A, BATCH_ITERS, lam, fit, workspace=ws)
+        out = {"members": len(shapes), "entries": entries, "bytes": 4 * entries, "precision": "fp32",
+               "als_iters": BATCH_ITERS,
+               "data": "N(0,1) tensors drawn on the device (seeded per member), shapes and ranks and ALS starts "
+                       "from the seeded workload generator; timing only"}
+        out["batched_call_ms"] = _time_component(batched, stream, reps=2)
+        out["per_member_calls_ms"] = _time_component(serial, stream, reps=1)
+        batched()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            reset()
+            cg.cp_als_batched(members, BATCH_ITERS, workspace=ws)
+        out["graph_replay_ms"] = _time_component(g.replay, stream, reps=2)
+        sweeps = len(shapes) * BATCH_ITERS
+        out["sweeps_per_s"] = sweeps / (out["batched_call_ms"] / 1e3)
+        out["two_pass_GBps"] = 2 * 4 * entries * BATCH_ITERS / (out["batched_call_ms"] / 1e3) / 1e9
+        out["two_pass_frac"] = out["two_pass_GBps"] / hbm
+        out["speedup_vs_per_member_calls"] = out["per_member_calls_ms"] / out["batched_call_ms"]
+        out["device_status"] = cg.cpg_device_status(ws)
+        del g
+        return out
+    run_config("batched_256", cbatch)
+    return res
 
 
 # ---- batched workload -------------------------------------------------------------------

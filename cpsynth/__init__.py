@@ -129,9 +129,16 @@ def make_problem(I: Sequence[int], R: int, *, snr_db: float | None = 20.0, seed:
 
 
 def random_tensor(I: Sequence[int], seed: int = DEFAULT_SEED, dtype=np.float32, stream: int = 5) -> np.ndarray:
-    """Plain N(0,1) tensor (no low-rank structure), vec layout."""
+    """Plain N(0,1) tensor (no low-rank structure), vec layout.  Drawn in
+    chunks (the same values as one draw of the whole length), so that a large
+    tensor never needs an FP64 copy."""
     g = rng(seed, stream)
-    return g.standard_normal(int(np.prod(I))).astype(dtype)
+    n = int(np.prod(I))
+    out = np.empty(n, dtype=dtype)
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        out[s:s + chunk] = g.standard_normal(min(chunk, n - s))
+    return out
 
 
 def random_factors(I: Sequence[int], R: int, seed: int = DEFAULT_SEED, dtype=np.float32,
@@ -157,17 +164,25 @@ def workload(name: str, seed: int = DEFAULT_SEED) -> Problem:
     return make_problem(I, R, snr_db=snr, seed=seed, dtype=dt, collinearity=col)
 
 
-def batched_workload(count: int = 256, seed: int = DEFAULT_SEED, orders=(3, 4, 5), size_range=(8, 64),
-                     rank_range=(4, 32), snr_db: float = 20.0, dtype=np.float32) -> list[Problem]:
-    """Many independent CP problems from one seed: order N uniform in
-    `orders`, every I_n uniform in `size_range` (inclusive), rank R uniform in
-    `rank_range` (inclusive), each a rank-R N(0,1) CP model plus Gaussian noise
-    at `snr_db`, with its own seeded ALS start."""
+def batched_shapes(count: int = 256, seed: int = DEFAULT_SEED, orders=(3, 4, 5), size_range=(8, 64),
+                   rank_range=(4, 32)) -> list[tuple[list[int], int]]:
+    """Shapes and ranks of the batched workload: order N uniform in `orders`,
+    every I_n uniform in `size_range` (inclusive), rank R uniform in
+    `rank_range` (inclusive), one (I, R) per member."""
     g = rng(seed, 77)
-    probs = []
-    for b in range(count):
+    out = []
+    for _ in range(count):
         N = int(g.choice(orders))
         I = [int(v) for v in g.integers(size_range[0], size_range[1] + 1, size=N)]
         R = int(g.integers(rank_range[0], rank_range[1] + 1))
-        probs.append(make_problem(I, R, snr_db=snr_db, seed=seed + 1 + b, dtype=dtype))
-    return probs
+        out.append((I, R))
+    return out
+
+
+def batched_workload(count: int = 256, seed: int = DEFAULT_SEED, orders=(3, 4, 5), size_range=(8, 64),
+                     rank_range=(4, 32), snr_db: float = 20.0, dtype=np.float32) -> list[Problem]:
+    """Many independent CP problems from one seed (shapes and ranks from
+    batched_shapes), each a rank-R N(0,1) CP model plus Gaussian noise at
+    `snr_db`, with its own seeded ALS start."""
+    return [make_problem(I, R, snr_db=snr_db, seed=seed + 1 + b, dtype=dtype)
+            for b, (I, R) in enumerate(batched_shapes(count, seed, orders, size_range, rank_range))]

@@ -319,20 +319,33 @@ int cpg_profile_read(float* ms, int* sides, int max);
  * CPG_NOALLOC_WORKSPACE_BYTES inside the library instead of opts->workspace.
  * precision and split are as in cpg_opts; stream is a cudaStream_t (NULL =
  * legacy default stream).
- *  - Returns CPG_ERR_WORKSPACE when cpg_workspace_size(I, N, R, ...,
- *    CPG_CALL_GRADIENT_ALL), less the optional pitched copy of Y it may
- *    include, exceeds CPG_NOALLOC_WORKSPACE_BYTES (without room for the copy
- *    the gradient streams Y itself), and the argument errors of
- *    cp_gradient_all otherwise; nothing is launched then.
+ *  - The argument errors of cp_gradient_all come first, in its order.  Then
+ *    CPG_ERR_WORKSPACE when the plan the call would run with that much room
+ *    (less the optional pitched copy of Y: without room for it the gradient
+ *    streams Y itself) exceeds CPG_NOALLOC_WORKSPACE_BYTES.  Nothing is
+ *    launched on an error.
  *  - The first call on a device looks up the array's device address (with
- *    that device current) and caches it; make that first call before any
- *    stream capture.
+ *    that device current), clears its device status word synchronously and
+ *    caches the address (thread-safe); make that first call, or one of
+ *    cpg_noalloc_scratch, before any stream capture.  The cached address is
+ *    not valid after cudaDeviceReset.
+ *  - Device-side conditions (a bounded wait that expired) are recorded in the
+ *    status word at the start of the array and kept until read: pass the
+ *    address from cpg_noalloc_scratch as opts->workspace to cpg_device_status.
  *  - Every call shares the one array and leaves its contents behind.  Calls
  *    that overlap on the GPU (different streams or threads) race on it;
  *    calls on one stream are ordered.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
 cpg_status cp_gradient_all_noalloc(const void* Y, const int64_t* I, int N, const void* const* A, int R,
                                    void* const* G, int precision, int split, void* stream);
+
+/* Device address (*ptr) and size (*bytes, may be NULL) of the fixed scratch
+ * array of cp_gradient_all_noalloc on the current device, set up as that
+ * call's first use on the device does.  With it a caller reads the array's
+ * device status word (cpg_device_status with opts->workspace = *ptr), or runs
+ * the bounded-wait self-test on it.  The paper has no counterpart.
+ * CPG_ERR_ARG for a NULL ptr, CPG_ERR_CUDA if the lookup fails. */
+cpg_status cpg_noalloc_scratch(void** ptr, size_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ Pins (all in ``tests/test_oracle.py``; none re-types the oracle's own code):
     fixed point, D never rises, factors stay nonnegative.
 """
 from .cp_oracle import (  # noqa: F401
-    unfold, khatri_rao, cp_gradient, cp_gradient_all, cp_gradient_entry,
+    unfold, khatri_rao, cp_gradient, cp_gradient_all, cp_gradient_entry, cp_gradient_entries,
     split_point, als_mode_order, gram_hadamard, cp_full, cp_fit_direct,
     cp_als, AlsTrace, cp_cost, cp_gradient_full, cp_gradient_step, cp_ntf, NtfTrace,
 )

@@ -74,12 +74,35 @@ def cp_gradient_entry(y: np.ndarray, I: Sequence[int], A: Sequence[np.ndarray], 
     unfold-and-multiply."""
     Y = as_tensor(y, I)
     N = len(I)
-    S = np.take(Y, i, axis=n)                       # (N-1)-D slice
+    S = Y[(slice(None),) * n + (i,)]                # (N-1)-D slice at i_n = i (a view)
     t = np.ones(1)
     for m in reversed(range(N)):
         if m != n:
             t = np.kron(t, A[m][:, r])
     return float(np.reshape(S, -1, order="F") @ t)
+
+
+def cp_gradient_entries(y: np.ndarray, I: Sequence[int], A: Sequence[np.ndarray], n: int,
+                        entries: Sequence[tuple[int, int]]) -> list[float]:
+    """Entries g_r^(n)[i] of eq. 3.2 for the (i, r) pairs given, as
+    cp_gradient_entry computes each one, but with each slice of Y at i_n = i
+    formed (in FP64) only once and without an FP64 copy of the whole tensor,
+    for tensors of several GB."""
+    I = [int(v) for v in I]
+    N = len(I)
+    Y = np.asarray(y).reshape(I, order="F")            # view, no copy
+    out, slices = [], {}
+    for i, r in entries:
+        if i not in slices:
+            slices.clear()
+            S = Y[(slice(None),) * n + (i,)]            # (N-1)-D slice at i_n = i (a view)
+            slices[i] = np.reshape(S, -1, order="F").astype(np.float64)
+        t = np.ones(1)
+        for m in reversed(range(N)):
+            if m != n:
+                t = np.kron(t, np.asarray(A[m], dtype=np.float64)[:, r])
+        out.append(float(slices[i] @ t))
+    return out
 
 
 def split_point(I: Sequence[int]) -> int:

@@ -167,16 +167,17 @@ int tc_code(int prec) {
 }
 
 // Grid over (J-blocks, K-splits): the K-split count that best fills `slots`
-// resident CTAs, discounting CTAs that run only a few stages.
-void choose_ksplit(LeadPlan& p, int slots) {
+// resident CTAs, discounting CTAs that run only a few stages; at most
+// max_per column chunks per CTA.
+void choose_ksplit(LeadPlan& p, int slots, int64_t max_per = INT64_MAX) {
   const int64_t chunks = (p.K + p.TK - 1) / p.TK;
   double best = -1.0;
   int best_ks = 1;
-  const int64_t max_ks = std::min<int64_t>(chunks, 4096);
+  const int64_t max_ks = std::min<int64_t>(chunks, 65535);
   for (int64_t ks = 1; ks <= max_ks; ++ks) {
     const int64_t per = (chunks + ks - 1) / ks;
     const int64_t nks = (chunks + per - 1) / per;
-    if (nks != ks) continue;
+    if (nks != ks || per > max_per) continue;
     const int64_t units = int64_t(p.nJb) * nks;
     if (units > 65535LL * 64) break;
     const int64_t waves = (units + slots - 1) / slots;
@@ -238,6 +239,13 @@ void choose_grid(LeadPlan& p, int R, int esize, int slots) {
   p.Kc = best_per * p.TK;
 }
 
+// The split-TF32 kernel accumulates a CTA's whole contraction range in tensor
+// memory, where each MMA's sum is rounded toward zero: its error grows about
+// linearly with the range (3.6e-6 relative at 704 columns, 3e-5 at 6579 on
+// the 100^4 workload).  Ranges are capped at this many contraction entries;
+// the partial sums of the ranges are added in FP32 round-to-nearest.
+constexpr int64_t kTf32MaxRun = 512;
+
 LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   LeadPlan p;
   p.tc = true;
@@ -258,6 +266,7 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
     // Minimise waves * (stages + W_L builds + fixed cost) + partial-sum
     // traffic, as choose_grid does for the CUDA-core kernel (1 CTA per SM).
     const int64_t max_per = std::max(1, tc_max_acc(p.RTP, 2, p.tc_prec));
+    const int64_t max_nrt = p.tc_prec == kTcTf32x3 ? std::max<int64_t>(1, kTf32MaxRun / p.TJ) : tiles;
     const int64_t chunks = (p.K + p.TK - 1) / p.TK;
     const int slots = num_sms();
     const double wbuild = 0.25 * p.RTP / 16.0;  // one W_L build, in super-stages
@@ -270,7 +279,7 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
       d = (q > 1) ? (tiles + q - 2) / (q - 1) : tiles + 1;
     }
     for (int64_t nrt : nrts)
-      for (int64_t per = 1; per <= std::min(max_per, chunks); ++per) {
+      for (int64_t per = 1; per <= std::min(max_per, chunks) && nrt <= max_nrt; ++per) {
         const int64_t nJb = (tiles + nrt - 1) / nrt, nCb = (chunks + per - 1) / per;
         if (nJb > 65535 || nCb > 65535) continue;
         const double waves = double((nJb * nCb + slots - 1) / slots);
@@ -291,7 +300,7 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
     const int cap = sides == 3 ? tc_fused_max_nrt(p.RTP, p.tc_prec) : std::min(tc_max_acc(p.RTP, 1, p.tc_prec), 8);
     p.nrt = int(std::max<int64_t>(1, std::min<int64_t>(tiles, cap)));
     p.nJb = int((p.J + int64_t(p.TJ) * p.nrt - 1) / (int64_t(p.TJ) * p.nrt));
-    choose_ksplit(p, num_sms());
+    choose_ksplit(p, num_sms(), p.tc_prec == kTcTf32x3 ? std::max<int64_t>(1, kTf32MaxRun / p.TK) : INT64_MAX);
   }
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
   p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
@@ -1414,6 +1423,22 @@ namespace cpg {
 size_t workspace_bytes_required(const int64_t* I, int N, int R, const cpg_opts* opts, int call) {
   return workspace_size_impl(I, N, R, opts, call, false);
 }
+
+cpg_status gradient_all_arg_status(const void* Y, const int64_t* I, int N, const void* const* A, int R,
+                                   void* const* G, const cpg_opts* opts) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N))
+    return CPG_ERR_ARG;
+  return CPG_OK;
+}
+
+size_t gradient_all_bytes_for(const int64_t* I, int N, int R, const cpg_opts* opts) {
+  Shape s;
+  if (opts == nullptr || common_checks(opts, s, I, N, R) != CPG_OK) return 0;
+  return grad_bytes(s, R, opts->precision, grad_choice(s, R, opts), false);
+}
 }  // namespace cpg
 
 extern "C" {
@@ -1430,11 +1455,10 @@ size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, 
 
 cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R, void* const* G,
                            const cpg_opts* opts) {
-  Shape s;
-  cpg_status st = common_checks(opts, s, I, N, R);
+  const cpg_status st = cpg::gradient_all_arg_status(Y, I, N, A, R, G, opts);
   if (st != CPG_OK) return st;
-  if (Y == nullptr || !ptrs_ok(A, N) || G == nullptr || !ptrs_ok(const_cast<const void* const*>(G), N))
-    return CPG_ERR_ARG;
+  Shape s;
+  check_shape(I, N, R, s);
   const GradChoice plan = grad_choice(s, R, opts);
   if (is_f64(opts->precision)) return gradient_all_impl<double>(s, static_cast<const double*>(Y), A, R, G, opts, plan);
   return gradient_all_impl<float>(s, static_cast<const float*>(Y), A, R, G, opts, plan);

@@ -14,6 +14,8 @@
 // race on it; calls issued on one stream are ordered and safe.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "../../include/cpgrad.h"
 #include "api_internal.h"
 
@@ -22,17 +24,23 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CPG_NOALLOC_WORKSPACE_BYTES];
 
 constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// array's name is only a host-side stand-in, so the address is looked up
+// with the device current, once per device (the first call on the device),
+// under a lock.  The same set-up clears the device status word at the start
+// of the array, synchronously: afterwards only cpg_device_status clears it.
+// The cached address is not valid after cudaDeviceReset.
 cpg_status scratch_for_current_device(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CPG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return CPG_ERR_CUDA;
+    if (cudaMemset(p, 0, 256) != cudaSuccess) return CPG_ERR_CUDA;
     g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
@@ -47,17 +55,26 @@ extern "C" cpg_status cp_gradient_all_noalloc(const void* Y, const int64_t* I, i
   o.precision = precision;
   o.split = split;
   o.stream = stream;
-  // The fixed array need not hold the optional pitched copy of Y: without
-  // room for it the gradient streams Y itself.
-  const size_t need = cpg::workspace_bytes_required(I, N, R, &o, CPG_CALL_GRADIENT_ALL);
+  // The argument errors of cp_gradient_all first, with nothing launched.
+  const cpg_status arg = cpg::gradient_all_arg_status(Y, I, N, A, R, G, &o);
+  if (arg != CPG_OK) return arg;
+  // The plan the call runs with this much room, without the optional pitched
+  // copy of Y (without room for it the gradient streams Y itself).
+  o.workspace_bytes = CPG_NOALLOC_WORKSPACE_BYTES;
+  const size_t need = cpg::gradient_all_bytes_for(I, N, R, &o);
   if (need == 0) return CPG_ERR_ARG;
   if (need > size_t(CPG_NOALLOC_WORKSPACE_BYTES)) return CPG_ERR_WORKSPACE;
   void* scratch = nullptr;
   const cpg_status st = scratch_for_current_device(&scratch);
   if (st != CPG_OK) return st;
   o.workspace = scratch;
-  o.workspace_bytes = CPG_NOALLOC_WORKSPACE_BYTES;
-  // The status word at the start of the array must read zero before use.
-  if (cudaMemsetAsync(scratch, 0, 256, static_cast<cudaStream_t>(stream)) != cudaSuccess) return CPG_ERR_CUDA;
   return cp_gradient_all(Y, I, N, A, R, G, &o);
+}
+
+extern "C" cpg_status cpg_noalloc_scratch(void** ptr, size_t* bytes) {
+  if (ptr == nullptr) return CPG_ERR_ARG;
+  const cpg_status st = scratch_for_current_device(ptr);
+  if (st != CPG_OK) return st;
+  if (bytes) *bytes = CPG_NOALLOC_WORKSPACE_BYTES;
+  return CPG_OK;
 }

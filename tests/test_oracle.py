@@ -78,6 +78,14 @@ def test_gradient_matches_bruteforce(I, R):
         for i in range(I[n]):
             for r in range(R):
                 assert oracle.cp_gradient_entry(y, I, A, n, i, r) == pytest.approx(Gb[i, r], rel=1e-12, abs=1e-12)
+        # the batched form (slices formed once, FP32 input as the large tests pass it)
+        pairs = [(i, r) for i in range(I[n]) for r in range(R)]
+        got = oracle.cp_gradient_entries(y, I, A, n, pairs)
+        np.testing.assert_allclose(got, [Gb[i, r] for i, r in pairs], rtol=1e-12, atol=1e-12)
+        y32 = y.astype(np.float32)
+        got32 = oracle.cp_gradient_entries(y32, I, A, n, pairs[::-1])
+        want32 = brute_gradient(y32.astype(np.float64), I, A, n)
+        np.testing.assert_allclose(got32, [want32[i, r] for i, r in pairs[::-1]], rtol=1e-12, atol=1e-12)
 
 
 def test_golden_worked_example():
@@ -299,3 +307,23 @@ def test_ntf_monotone_nonnegative_and_fit_formula():
         assert all(np.all(a >= 0) for a in A)
         assert abs(tr.fits[-1] - oracle.cp_fit_direct(y, A, np.ones(R))) <= 1e-9
         D = Dn
+
+
+def test_sweep_backward_error_check():
+    """The ALS parity check (tests/als_checks.py): zero for the oracle's own
+    sweep, the size of the error for a planted one, and independent of the
+    column scales that normalisation removes."""
+    from als_checks import sweep_backward_errors
+    I, R = [7, 6, 5, 4], 3
+    p = cpsynth.make_problem(I, R, snr_db=20.0, seed=17, dtype=np.float64)
+    tr = oracle.cp_als(p.y, I, p.init, iters=1)
+    errs = sweep_backward_errors(p.y, I, p.init, tr.A)
+    assert set(errs) == set(range(len(I)))
+    assert max(errs.values()) <= 1e-12, errs
+    scaled = [a * np.array([2.0, 0.5, 3.0])[None, :] for a in tr.A]
+    assert max(sweep_backward_errors(p.y, I, p.init, scaled).values()) <= 1e-12
+    for n in range(len(I)):
+        bad = [a.copy() for a in tr.A]
+        bad[n][0, 0] += 1e-3 * np.linalg.norm(bad[n])
+        e = sweep_backward_errors(p.y, I, p.init, bad)
+        assert e[n] > 1e-5, (n, e)
