@@ -123,8 +123,12 @@ int cpg_split_point(const int64_t* I, int N);
 size_t cpg_workspace_size(const int64_t* I, int N, int R, const cpg_opts* opts, int call);
 
 /* All-mode CP gradient, Algorithm 2 (Section 3.3): G[n] <- Y_(n) KR_{m != n}
- * for every n in [0, N).  One pass over Y computes both leading
- * contractions (steps 4 and 7) from each tile; the other modes follow from
+ * for every n in [0, N).  The two leading contractions (steps 4 and 7) are
+ * computed from one pass over Y (both from each tile) or from two, one per
+ * side: the measured plan of cpg_autotune_gradient when one is recorded,
+ * else the planner's, which fuses the CUDA-core passes only at R <= 4 and the
+ * tensor-core passes for BF16 and BF16x3 at R <= 32, when the partial sums of
+ * the fused pass stay below a fifth of Y's size.  The other modes follow from
  * R^(n) and L^(n) (steps 11, 15, 19, 20).  G[n] are overwritten. */
 cpg_status cp_gradient_all(const void* Y, const int64_t* I, int N, const void* const* A, int R,
                            void* const* G, const cpg_opts* opts);
@@ -175,7 +179,8 @@ cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* 
  * Each update solves A^(n) V = G^(n), V = Hadamard_{m != n} A^(m)T A^(m)
  * (Gauss-Jordan inverse of V in double-float arithmetic for FP32 data, FP64
  * Cholesky for FP64 data), then normalises the columns: lambda_r =
- * ||a_r^(n)||, a_r^(n) /= lambda_r.  R <= 64.  A[n] (device, I_n x R) and lambda (device, R
+ * ||a_r^(n)||, a_r^(n) /= lambda_r.  R <= 64 (the gradient calls take up to CPG_MAX_RANK;
+ * a larger R here returns CPG_ERR_UNSUPPORTED).  A[n] (device, I_n x R) and lambda (device, R
  * doubles) are updated in place; A on entry is the starting point.
  * fit (device, `iters` doubles, may be NULL) receives after each sweep
  * fit = 1 - ||Y - Yhat||_F / ||Y||_F computed from R x R quantities.

@@ -316,6 +316,14 @@ LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
   p.J = prod(s, 0, k);
   p.K = prod(s, k, s.N);
   p.RTmax = is_f64(prec) ? kMaxRankTileF64 : kMaxRankTileF32;
+  // FP32 step 4 copies Khatri-Rao rows built once per pass only up to rank 32
+  // (above, a stage's rows outweigh half its tile and every CTA generates its
+  // own: 0.33 TB/s at R = 64 on 60^5, against 2.7 TB/s at R = 32).  Wider
+  // ranks run as balanced groups of at most 32, one pass over Y each.
+  if (!is_f64(prec) && sides == 1 && R > 32) {
+    const int ng = (R + 31) / 32;
+    p.RTmax = (R + ng - 1) / ng;
+  }
   p.groups = (R + p.RTmax - 1) / p.RTmax;
   // All rank groups share one tile geometry: the widest group's.
   const SimtShape sh = shape_for(prec, std::min(R, p.RTmax), sides);

@@ -100,3 +100,40 @@ def test_batched_is_ordered_on_the_caller_stream(cg):
     s.synchronize()
     for b in range(len(probs)):
         assert torch.equal(snap[b], A_b[b][0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_batched_graph_replay(cg, prec):
+    """One cp_als_batched call captured in a CUDA graph (the pool streams are
+    forked from and joined into the capturing stream) and replayed twice:
+    bitwise the results of the same call made directly."""
+    probs = mixed_batch(12, seed=19, dtype=np.float32)
+    iters = 3
+    Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+    A0 = [[dev_factor(a, np.float32) for a in p.init] for p in probs]
+    A_ref = [[a.clone() for a in A] for A in A0]
+    ref = cg.cp_als_batched([(Y, p.I, A) for Y, p, A in zip(Ys, probs, A_ref)], iters, precision=prec)
+    torch.cuda.synchronize()
+    # buffers the graph reads and writes, allocated before the capture
+    A_g = [[a.clone() for a in A] for A in A0]
+    lams = [torch.ones(p.R, dtype=torch.float64, device="cuda") for p in probs]
+    fits = [torch.zeros(iters, dtype=torch.float64, device="cuda") for _ in probs]
+    members = [(Y, p.I, A, lam, fit) for Y, p, A, lam, fit in zip(Ys, probs, A_g, lams, fits)]
+    ws = cg.Workspace()
+    cg.cp_als_batched(members, iters, precision=prec, workspace=ws)  # sizes the workspace, creates the pool
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for A, A_init in zip(A_g, A0):
+            for a, a0 in zip(A, A_init):
+                a.copy_(a0)
+        cg.cp_als_batched(members, iters, precision=prec, workspace=ws)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        for b in range(len(probs)):
+            for a1, a2 in zip(A_g[b], A_ref[b]):
+                assert torch.equal(a1, a2), b
+            assert torch.equal(lams[b], ref[b][0]), b
+            assert torch.equal(fits[b], ref[b][1]), b
+    assert cg.cpg_device_status(ws) == 0
