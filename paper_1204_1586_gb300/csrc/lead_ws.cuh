@@ -140,6 +140,12 @@ struct WsCfg {
   static constexpr int NSLOT = (2 * NSIDE * NW <= 512 - 2 * RTP) ? 2 : 1;
   static constexpr int SLOT_COLS = NSIDE * NSLOT * NW;
   static constexpr int MAX_ACC = (512 - SLOT_COLS) / RTP;
+  // One side with as many limb stages as slots: "stage ss's MMAs completed"
+  // frees limb stage ss % NL and fills slot ss % NSLOT at once, so one
+  // barrier (limb_empty) carries both.  Its phases cannot run ahead of either
+  // waiter: the MMAs of stage ss + NL need the converters' stage ss + NL and
+  // the promotion's release of slot ss.
+  static constexpr bool ONE_COMMIT = NSIDE == 1 && NL == NSLOT;
   static constexpr int NEXP = 8;                    // ring of per-tile scale exponents
 };
 
@@ -344,9 +350,20 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
   } else if (warp == 1) {
     // ---- MMA issuer -----------------------------------------------------------------
     if (lane == 0) {
-      int mmas = 0;
+      // This one thread bounds the pass when its loop is long (a stage's MMAs
+      // wait for its scalar work), so the loop is kept short: the stage
+      // coordinates advance by counters, and every shared-memory descriptor is
+      // a base descriptor built once plus a constant offset.  The start-address
+      // field holds address >> 4 and every shared address here is below 2^18,
+      // so adding offset >> 4 cannot carry out of the field.
+      const uint32_t limb0 = tc::smem_addr(sm + C::OFF_LIMB);
+      const uint64_t a_r0 = tc::smem_desc_sw128(limb0, 1024, NH * 1024);  // step 4: MN-major A
+      const uint64_t a_l0 = tc::smem_desc_sw128(limb0, 16, NH * 1024);    // step 7: K-major A
+      const uint64_t b_r0 = tc::smem_desc_sw128(tc::smem_addr(sm + C::OFF_WR), 16, (C::KWR / 64) * 1024);
+      const uint64_t b_l0 = tc::smem_desc_sw128(tc::smem_addr(sm + C::OFF_WL), 16, (C::KWL / 64) * 1024);
+      const uint32_t dslot = tbase + slot0;
+      int q = 0, rt = 0;  // chunk and row tile of stage ss
       for (int ss = 0; ss < nss; ++ss) {
-        const int q = chunk_of(ss), rt = tile_of(ss);
         const int ls = ss % NL, sl = ss % NSLOT;
         if constexpr (DO_R) {
           if (!ws_wait(&wr_full[q % WBR], uint32_t(q / WBR) & 1u, abort)) break;
@@ -363,51 +380,61 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
             ok = ws_wait(&slot_empty[s][sl], uint32_t(ss / NSLOT - 1) & 1u, abort);
         if (!ok) break;
         tc::tc_fence_after();
-        const uint32_t limb = tc::smem_addr(sm + C::OFF_LIMB + ls * C::STAGE_BYTES);
+        const uint64_t aoff = uint64_t(ls * C::STAGE_BYTES) >> 4;
         int side = 0;
         if constexpr (DO_R) {
           // Step 4: D[j, n] += A[j, c] B[n, c]; A MN-major (K step = 2 column groups).
-          const uint32_t w0 = tc::smem_addr(sm + C::OFF_WR + (q % WBR) * C::WR_BYTES);
-          const uint32_t d = tbase + slot0 + uint32_t((side * NSLOT + sl) * NW);
+          const uint64_t ar = a_r0 + aoff, br = b_r0 + (uint64_t((q % WBR) * C::WR_BYTES) >> 4);
+          const uint32_t d = dslot + uint32_t((side * NSLOT + sl) * NW);
 #pragma unroll
           for (int s = 0; s < SC / 16; ++s) {
-            const uint64_t bd = tc::smem_desc_sw128(w0 + (s >> 2) * 1024 + (s & 3) * 32, 16, (C::KWR / 64) * 1024);
 #pragma unroll
             for (int l = 0; l < L; ++l)
-              ws_mma(d, tc::smem_desc_sw128(limb + l * C::LIMB_BYTES + s * 2 * NH * 1024, 1024, NH * 1024), bd,
-                     tc::idesc_bf16_f32(128, (L - l) * RTP, 1, 0), (s > 0 || l > 0) ? 1u : 0u);
+              ws_mma(d, ar + uint64_t((l * C::LIMB_BYTES + s * 2 * NH * 1024) >> 4),
+                     br + uint64_t(((s >> 2) * 1024 + (s & 3) * 32) >> 4), tc::idesc_bf16_f32(128, (L - l) * RTP, 1, 0),
+                     (s > 0 || l > 0) ? 1u : 0u);
           }
           ++side;
         }
         if constexpr (DO_L) {
           // Step 7: D[c, n] += A[c, j] B[n, j]; A K-major (K step = 32 bytes of a line).
           const int wl = SIDES == 2 ? rt % WBL : rt;
-          const uint32_t w0 = tc::smem_addr(sm + C::OFF_WL + wl * C::WL_BYTES);
-          const uint32_t d = tbase + slot0 + uint32_t((side * NSLOT + sl) * NW);
+          const uint64_t al = a_l0 + aoff, bl = b_l0 + (uint64_t(wl * C::WL_BYTES) >> 4);
+          const uint32_t d = dslot + uint32_t((side * NSLOT + sl) * NW);
 #pragma unroll
           for (int s = 0; s < SR / 16; ++s) {
-            const uint32_t koff = (s >> 2) * 1024 + (s & 3) * 32;
-            const uint64_t bd = tc::smem_desc_sw128(w0 + koff, 16, (C::KWL / 64) * 1024);
+            const int koff = (s >> 2) * 1024 + (s & 3) * 32;
 #pragma unroll
             for (int l = 0; l < L; ++l)
-              ws_mma(d, tc::smem_desc_sw128(limb + l * C::LIMB_BYTES + koff, 16, NH * 1024), bd,
+              ws_mma(d, al + uint64_t((l * C::LIMB_BYTES + koff) >> 4), bl + uint64_t(koff >> 4),
                      tc::idesc_bf16_f32(128, (L - l) * RTP, 0, 0), (s > 0 || l > 0) ? 1u : 0u);
           }
         }
         tc::mma_commit(&limb_empty[ls]);
-        for (int s = 0; s < C::NSIDE; ++s) tc::mma_commit(&slot_full[s][sl]);
+        if constexpr (!C::ONE_COMMIT)
+          for (int s = 0; s < C::NSIDE; ++s) tc::mma_commit(&slot_full[s][sl]);
         if constexpr (DO_R) {
           if (rt == nrt - 1) tc::mma_commit(&wr_empty[q % WBR]);
         }
         if constexpr (SIDES == 2) {
           if (q == nchunk - 1) tc::mma_commit(&wl_empty[rt % WBL]);
         }
-        ++mmas;
+        // next stage's coordinates (the loop order of chunk_of / tile_of)
+        if constexpr (ROWS_OUTER) {
+          if (++q == nchunk) {
+            q = 0;
+            ++rt;
+          }
+        } else {
+          if (++rt == nrt) {
+            rt = 0;
+            ++q;
+          }
+        }
       }
       // Every MMA this thread issued has completed once mma_done flips.
       tc::mma_commit(&mma_done);
       tc::mbar_wait(&mma_done, 0u, 1u << 20);
-      (void)mmas;
     }
   } else if (warp < 6) {
     // ---- promotion ------------------------------------------------------------------
@@ -439,7 +466,7 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
       for (int sd = 0; sd < 2; ++sd) {
         const bool is_r = sd == 0;
         if (is_r ? !DO_R : !DO_L) continue;
-        if (!ws_wait(&slot_full[side][sl], uint32_t(ss / NSLOT) & 1u, abort)) break;
+        if (!ws_wait(C::ONE_COMMIT ? &limb_empty[sl] : &slot_full[side][sl], uint32_t(ss / NSLOT) & 1u, abort)) break;
         // Scale exponents of the stage's B tile.
         const signed char* ex;
         if (is_r) {
