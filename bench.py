@@ -313,6 +313,9 @@ def main():
     # The gradient's plan (split k, fused or two passes) is measured once on
     # this data before the warm-up, outside the timed region.
     plan = cg.cp_gradient_autotune(Y, I, A0, G, precision=prec, workspace=ws, reps=3)
+    # So is the CP_ALS sweep's split (A0 keeps its values).
+    als_plan = cg.cp_als_autotune(Y, I, A0, precision=prec, workspace=ws, reps=3) \
+        if prec not in GRAD_ONLY_PRECS else None
     for _ in range(args.warmup):
         step(Y)
     barrier()
@@ -452,6 +455,8 @@ def main():
                    "I": I, "R": R, "split_k": split_point(I), "precision": prec, "als_iters": ALS_ITERS,
                    "gradient_plan": {"split": plan["split"], "fused": plan["fused"], "tuned_ms": plan["ms"],
                                      "candidates": plan["candidates"]},
+                   "als_plan": None if als_plan is None else {"split": als_plan["split"], "tuned_ms": als_plan["ms"],
+                                                              "candidates": als_plan["candidates"]},
                    "l2": "inputs larger than L2 (400 MB tensor)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "gradient_gflops": gradient_flops(I, R) / 1e9,
         "als_iter_per_s": None,
@@ -548,6 +553,8 @@ def _measure_case(cg, Y, I, A0, G, ws, stream, prec, hbm, esize=4):
     cg.cp_gradient_all(Y, I, A0, G, workspace=ws, precision=prec)
     passes = {}
     if prec not in GRAD_ONLY_PRECS:
+        ap = cg.cp_als_autotune(Y, I, A0, precision=prec, workspace=ws, reps=2)
+        out["als_plan"] = {"split": ap["split"], "candidates": ap["candidates"]}
         ta = _time_component(lambda: cg.cp_als_iter(Y, I, [a.clone() for a in A0], 5, workspace=ws, precision=prec),
                              stream) / 5
         out["als_sweep_ms"] = ta
@@ -692,8 +699,23 @@ def measure_configs(cg, dev, stream, hbm, batch_count):
                "als_iters": BATCH_ITERS,
                "data": "N(0,1) tensors drawn on the device (seeded per member), shapes and ranks and ALS starts "
                        "from the seeded workload generator; timing only"}
+        out["batched_call_ms_nstar"] = _time_component(batched, stream, reps=2)
+        # the CP_ALS split of every member, measured (A and lambda keep their values)
+        t0 = time.time()
+        off = 0
+        for Y, I, A, lam, _ in members:
+            off += cg.cp_als_autotune(Y, I, A, lam, workspace=ws, reps=1)["split"] != cg.cpg_split_point(I)
+        torch.cuda.synchronize()
+        out["als_autotune"] = {"seconds": round(time.time() - t0, 2), "members_not_at_nstar": int(off)}
         out["batched_call_ms"] = _time_component(batched, stream, reps=2)
         out["per_member_calls_ms"] = _time_component(serial, stream, reps=1)
+
+        def batched_x6():
+            reset()
+            cg.cp_als_batched(members, BATCH_ITERS, workspace=ws, precision="bf16x6")
+        for Y, I, A, lam, _ in members:
+            cg.cp_als_autotune(Y, I, A, lam, workspace=ws, reps=1, precision="bf16x6")
+        out["batched_call_ms_bf16x6"] = _time_component(batched_x6, stream, reps=2)
         batched()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()

@@ -102,7 +102,8 @@ typedef enum {
   CPG_CALL_ALS = 2,
   CPG_CALL_GRADIENT_TUNE = 3,
   CPG_CALL_GRADIENT_FULL = 4,  /* cp_gradient_full and cp_gradient_step */
-  CPG_CALL_NTF = 5             /* cp_ntf_iter */
+  CPG_CALL_NTF = 5,            /* cp_ntf_iter */
+  CPG_CALL_ALS_TUNE = 6        /* cpg_autotune_als */
 } cpg_call;
 
 /* n* = max{n : J_n <= K_n} of Algorithm 2 step 1, 1-based count of leading
@@ -165,8 +166,48 @@ cpg_status cpg_autotune_gradient(const void* Y, const int64_t* I, int N, const v
  * rank and opts (precision, split, current device); 0 otherwise.  Host-only. */
 int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_gradient_plan* plan);
 
-/* Forgets every recorded plan. */
+/* Forgets every recorded plan (gradient plans and CP_ALS splits). */
 void cpg_autotune_clear(void);
+
+/* The split of a CP_ALS sweep: k leading modes, update order k-1, ..., 0,
+ * k, ..., N-1 (Section 4 with n* replaced by k). */
+typedef struct {
+  int split;       /* 1 <= split <= N-1                              */
+  float ms;        /* measured milliseconds per sweep (autotune only) */
+  int candidates;  /* splits timed (autotune only)                    */
+} cpg_als_plan;
+
+/* Splits cpg_autotune_als times, cheapest modelled first: opts->split alone
+ * when nonzero, else n* (Algorithm 2 step 1) and every k in [1, N-1] whose
+ * modelled sweep cost is within 1.25x of the cheapest.  The model counts the elements a sweep moves: two
+ * reads of Y (the same for every k), the Khatri-Rao operands of the two
+ * passes, and twice (written, read) every partial result R^(m), m <= k, and
+ * L^(m), m > k, of the recursions (steps 11 and 15 of Algorithm 2), which
+ * are also the sizes Table 4.1's multiplication counts sum.  Writes up to
+ * `cap` splits to `splits` (may be NULL) and returns how many there are;
+ * 0 on invalid arguments.  Host-only. */
+int cpg_als_candidates(const int64_t* I, int N, int R, const cpg_opts* opts, int* splits, int cap);
+
+/* Measured choice of the CP_ALS split.  Each candidate of cpg_als_candidates
+ * runs one untimed sweep, then `reps` sweeps (1..1000) between CUDA events on
+ * opts->stream, each from the caller's starting A and lambda, which are saved
+ * in the workspace first and restored after every run: on return A and lambda
+ * hold their entry values.  The call synchronizes the stream, so it cannot be
+ * captured in a CUDA graph.  The fastest split is recorded for this device,
+ * precision, requested split, rank and shape (process-wide, thread-safe) and
+ * written to *chosen (may be NULL).  Later cp_als_iter and cp_ntf_iter calls
+ * with opts->split == 0 and the same key run the recorded split whenever
+ * their workspace holds it (cpg_workspace_size accounts for it; so do the
+ * members of cp_als_batched), else n*.  Workspace:
+ * cpg_workspace_size(..., CPG_CALL_ALS_TUNE) bytes, else CPG_ERR_WORKSPACE;
+ * argument and precision errors as for cp_als_iter. */
+cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
+                            const cpg_opts* opts, int reps, cpg_als_plan* chosen);
+
+/* 1 and *plan (split) when a measured CP_ALS split is recorded for this
+ * shape, rank and opts (precision, split, current device); 0 otherwise.
+ * Host-only. */
+int cpg_als_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_als_plan* plan);
 
 /* Single-mode CP gradient, Section 3.2: G^(n) via the right-to-left route
  * (eqs. 3.7, 3.10, 3.12) when J_n <= K_{n-1}, else the left-to-right route
@@ -175,7 +216,8 @@ cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* 
                             int n, void* Gn, const cpg_opts* opts);
 
 /* `iters` sweeps of the fast CP_ALS of Section 4 with update rule eq. 2.14.
- * Mode order per sweep (0-based, k = split): k-1, k-2, ..., 0, k, ..., N-1.
+ * Mode order per sweep (0-based): k-1, k-2, ..., 0, k, ..., N-1, with k =
+ * opts->split, else the split cpg_autotune_als recorded, else n*.
  * Each update solves A^(n) V = G^(n), V = Hadamard_{m != n} A^(m)T A^(m)
  * (Gauss-Jordan inverse of V in double-float arithmetic for FP32 data, FP64
  * Cholesky for FP64 data), then normalises the columns: lambda_r =

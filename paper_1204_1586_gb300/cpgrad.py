@@ -22,12 +22,13 @@ LIB_PATH = os.path.join(_HERE, "libcpgrad.so")
 CPG_OK, CPG_ERR_ARG, CPG_ERR_SHAPE, CPG_ERR_WORKSPACE, CPG_ERR_SINGULAR, CPG_ERR_CUDA, CPG_ERR_TIMEOUT, \
     CPG_ERR_UNSUPPORTED = range(8)
 PRECISIONS = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16": 3, "fp64": 4, "bf16x6": 5}
-CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE, CALL_GRADIENT_FULL, CALL_NTF = 0, 1, 2, 3, 4, 5
+CALL_GRADIENT_ALL, CALL_GRADIENT_MODE, CALL_ALS, CALL_GRADIENT_TUNE, CALL_GRADIENT_FULL, CALL_NTF, CALL_ALS_TUNE = \
+    range(7)
 EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradient_mode", "cp_als_iter",
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
            "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read", "cpg_autotune_gradient",
            "cpg_gradient_plan_query", "cpg_autotune_clear", "cp_gradient_full", "cp_gradient_step", "cp_ntf_iter",
-           "cpg_selftest_timeout"]
+           "cpg_selftest_timeout", "cpg_als_candidates", "cpg_autotune_als", "cpg_als_plan_query"]
 
 
 class CpgError(RuntimeError):
@@ -43,6 +44,10 @@ class cpg_opts(ctypes.Structure):
 
 class cpg_gradient_plan(ctypes.Structure):
     _fields_ = [("split", ctypes.c_int), ("fused", ctypes.c_int), ("ms", ctypes.c_float), ("candidates", ctypes.c_int)]
+
+
+class cpg_als_plan(ctypes.Structure):
+    _fields_ = [("split", ctypes.c_int), ("ms", ctypes.c_float), ("candidates", ctypes.c_int)]
 
 
 class cpg_tensor_desc(ctypes.Structure):
@@ -102,6 +107,15 @@ def lib() -> ctypes.CDLL:
         L.cpg_gradient_plan_query.restype = ctypes.c_int
         L.cpg_autotune_clear.argtypes = []
         L.cpg_autotune_clear.restype = None
+        L.cpg_als_candidates.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.cpg_als_candidates.restype = ctypes.c_int
+        L.cpg_autotune_als.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.POINTER(cpg_opts), ctypes.c_int, ctypes.POINTER(cpg_als_plan)]
+        L.cpg_autotune_als.restype = ctypes.c_int
+        L.cpg_als_plan_query.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
+                                         ctypes.POINTER(cpg_als_plan)]
+        L.cpg_als_plan_query.restype = ctypes.c_int
         L.cp_gradient_full.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, vpp,
                                        ctypes.POINTER(cpg_opts)]
         L.cp_gradient_full.restype = ctypes.c_int
@@ -413,6 +427,49 @@ def cp_als_iter(Y, I: Sequence[int], A, iters: int, lam=None, fit=None, *, preci
     if st != CPG_OK:
         raise CpgError(st, "cp_als_iter")
     return lam, fit
+
+
+def als_candidates(I: Sequence[int], R: int, precision="fp32", split: int = 0):
+    """The splits the CP_ALS autotuner times, cheapest modelled first (host only)."""
+    o = cpg_opts(_prec(precision), int(split), None, 0, None)
+    buf = (ctypes.c_int * 64)()
+    n = lib().cpg_als_candidates(_i64(I), len(I), int(R), ctypes.byref(o), buf, 64)
+    if n == 0:
+        raise CpgError(CPG_ERR_ARG, "cpg_als_candidates")
+    return [int(buf[i]) for i in range(min(n, 64))]
+
+
+def cp_als_autotune(Y, I: Sequence[int], A, lam=None, *, precision="fp32", split: int = 0, reps: int = 2,
+                    workspace=None, stream=None):
+    """Times CP_ALS sweeps at each candidate split on these inputs and records
+    the fastest for later cp_als_iter / cp_ntf_iter / cp_als_batched calls of
+    this shape, rank and precision.  A and lam keep their entry values.
+    Returns {"split", "ms", "candidates"}."""
+    torch = _torch()
+    R = int(A[0].shape[1])
+    dtype = torch.float64 if _prec(precision) == PRECISIONS["fp64"] else torch.float32
+    _check_y(Y, I, dtype)
+    for m, a in enumerate(A):
+        _check_colmajor(a, int(I[m]), R, dtype, f"A[{m}]")
+    if lam is None:
+        lam = torch.ones(R, dtype=torch.float64, device=Y.device)
+    ws = _ws_for(workspace, Y.device)
+    o = _opts(precision, split, ws, cpg_workspace_size(I, R, precision, split, CALL_ALS_TUNE), _stream_ptr(stream))
+    plan = cpg_als_plan()
+    st = lib().cpg_autotune_als(ctypes.c_void_p(Y.data_ptr()), _i64(I), len(I), _ptrs(A),
+                                ctypes.c_void_p(lam.data_ptr()), R, ctypes.byref(o), int(reps), ctypes.byref(plan))
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_autotune_als")
+    return {"split": plan.split, "ms": float(plan.ms), "candidates": plan.candidates}
+
+
+def als_plan(I: Sequence[int], R: int, precision="fp32", split: int = 0):
+    """The recorded measured CP_ALS split for this shape / rank / precision, or None."""
+    o = cpg_opts(_prec(precision), int(split), None, 0, None)
+    plan = cpg_als_plan()
+    if not lib().cpg_als_plan_query(_i64(I), len(I), int(R), ctypes.byref(o), ctypes.byref(plan)):
+        return None
+    return plan.split
 
 
 def cp_als_batched(members, iters: int, *, precision="fp32", split: int = 0, workspace=None, stream=None):

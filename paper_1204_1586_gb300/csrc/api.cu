@@ -927,6 +927,73 @@ GradChoice grad_choice(const Shape& s, int R, const cpg_opts* o) {
   return default_choice(s, R, o);
 }
 
+// ---- split of the CP_ALS sweep --------------------------------------------------------
+// Workspace bytes of a CP_ALS (or NTF) sweep at split k.
+size_t als_bytes(const Shape& s, int R, int prec, int k, bool with_copy) {
+  const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
+  const size_t ypn = with_copy ? pitched_elems(lr.J, lr.K, is_f64(prec) ? 8 : 4) : 0;
+  size_t bytes = 0;
+  if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes, ypn);
+  else carve_als<float>(nullptr, s, R, lr, ll, &bytes, ypn);
+  return bytes;
+}
+
+// Modelled cost of one sweep at split k (1-based count of leading modes), in
+// elements moved: the two passes over Y (Algorithm 2 steps 4 and 7, the same
+// for every k), the Khatri-Rao operands of the passes, and the recursions of
+// steps 11 and 15 with their finishing contractions (steps 19 and 20), which
+// read R^(m) (J_m x R, m <= k) and L^(m) (R x K_(m-1), m > k) and whose
+// multiplication counts Table 4.1 sums the same way.  Partial results are
+// written once and read once.
+double als_model_cost(const Shape& s, int R, int k) {
+  std::vector<double> J(s.N + 1, 1.0), K(s.N + 1, 1.0);  // J[m] = I_0..I_(m-1), K[m] = I_m..I_(N-1)
+  for (int m = 1; m <= s.N; ++m) J[m] = J[m - 1] * double(s.I[m - 1]);
+  for (int m = s.N - 1; m >= 0; --m) K[m] = K[m + 1] * double(s.I[m]);
+  double side = J[k] + K[k];  // Khatri-Rao operands of the two passes
+  for (int m = 1; m <= k; ++m) side += 2.0 * J[m];
+  for (int m = k; m < s.N; ++m) side += 2.0 * K[m];
+  return 2.0 * double(s.total) + double(R) * side;
+}
+
+// Splits the ALS autotuner times: opts->split alone when set, else n*
+// (Algorithm 2 step 1) and every k whose modelled cost is within 1.25x of
+// the cheapest, cheapest first.
+std::vector<int> als_candidates(const Shape& s, int R, const cpg_opts* o) {
+  if (o && o->split != 0) return {o->split};
+  std::vector<std::pair<double, int>> c;
+  double best = 0.0;
+  for (int k = 1; k <= s.N - 1; ++k) {
+    const double m = als_model_cost(s, R, k);
+    c.push_back({m, k});
+    if (k == 1 || m < best) best = m;
+  }
+  std::stable_sort(c.begin(), c.end());
+  std::vector<int> v;
+  for (const auto& e : c)
+    if (e.first <= 1.25 * best || e.second == split_point(s)) v.push_back(e.second);
+  return v;
+}
+
+// Measured splits (cpg_autotune_als), keyed like the gradient's plans.
+std::map<std::vector<int64_t>, int> g_als_tuned;
+
+bool tuned_als_split(const Shape& s, int R, const cpg_opts* o, int* k) {
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  auto it = g_als_tuned.find(tune_key(s, R, o));
+  if (it == g_als_tuned.end()) return false;
+  *k = it->second;
+  return true;
+}
+
+// The split a sweep runs: the requested one, else the measured one when the
+// workspace holds it, else n*.
+int als_split(const Shape& s, int R, const cpg_opts* o) {
+  if (o->split != 0) return o->split;
+  int k = 0;
+  if (tuned_als_split(s, R, o, &k) && o->workspace_bytes >= als_bytes(s, R, o->precision, k, false)) return k;
+  return split_point(s);
+}
+
 // ---- all-mode gradient (Algorithm 2) ------------------------------------------------
 template <typename T>
 cpg_status gradient_all_impl(const Shape& s, const T* Y, const void* const* A, int R, void* const* G,
@@ -1096,7 +1163,7 @@ cpg_status als_impl(const Shape& s, const T* Y, void* const* A, double* lambda, 
                     const cpg_opts* o, int* status_override = nullptr, bool mu = false) {
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
   if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
-  const int k = choose_split(s, o);
+  const int k = als_split(s, R, o);
   const LeadPlan lr = plan_lead(s, R, k, 1, o->precision);
   const LeadPlan ll = plan_lead(s, R, k, 2, o->precision);
   // A copy of Y with a 16-byte column pitch when Y's own pitch is not one and
@@ -1383,6 +1450,15 @@ bool ptrs_ok(const void* const* P, int N) {
   return true;
 }
 
+// The ALS autotuner keeps the caller's factors and lambda after the largest
+// candidate's workspace.
+size_t als_tune_save_offset(size_t als_need) { return align_up(als_need); }
+size_t als_tune_save_bytes(const Shape& s, int R, int prec) {
+  size_t e = 0;
+  for (int n = 0; n < s.N; ++n) e += size_t(s.I[n]) * size_t(R);
+  return align_up(e * (is_f64(prec) ? 8 : 4)) + size_t(R) * sizeof(double);
+}
+
 // Workspace bytes of `call`; with_copy: including the optional pitched copy of Y.
 size_t workspace_size_impl(const int64_t* I, int N, int R, const cpg_opts* opts, int call, bool with_copy) {
   Shape s;
@@ -1415,10 +1491,13 @@ size_t workspace_size_impl(const int64_t* I, int N, int R, const cpg_opts* opts,
       bytes = std::max(bytes, b);
     }
   } else if (call == CPG_CALL_ALS || call == CPG_CALL_NTF) {
-    const LeadPlan lr = plan_lead(s, R, k, 1, prec), ll = plan_lead(s, R, k, 2, prec);
-    const size_t ypn = with_copy ? pitched_elems(lr.J, lr.K, is_f64(prec) ? 8 : 4) : 0;
-    if (is_f64(prec)) carve_als<double>(nullptr, s, R, lr, ll, &bytes, ypn);
-    else carve_als<float>(nullptr, s, R, lr, ll, &bytes, ypn);
+    bytes = als_bytes(s, R, prec, k, with_copy);
+    int t = 0;
+    if ((!opts || opts->split == 0) && tuned_als_split(s, R, &od, &t))
+      bytes = std::max(bytes, als_bytes(s, R, prec, t, with_copy));
+  } else if (call == CPG_CALL_ALS_TUNE) {
+    for (int c : als_candidates(s, R, &od)) bytes = std::max(bytes, als_bytes(s, R, prec, c, with_copy));
+    bytes = als_tune_save_offset(bytes) + als_tune_save_bytes(s, R, prec);
   } else {
     return 0;
   }
@@ -1544,6 +1623,110 @@ int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts
 void cpg_autotune_clear(void) {
   std::lock_guard<std::mutex> lock(g_tuned_mu);
   g_tuned.clear();
+  g_als_tuned.clear();
+}
+
+int cpg_als_candidates(const int64_t* I, int N, int R, const cpg_opts* opts, int* splits, int cap) {
+  Shape s;
+  if (check_shape(I, N, R, s) != CPG_OK || (opts && opts->split != 0 && (opts->split < 1 || opts->split > N - 1)))
+    return 0;
+  const std::vector<int> c = als_candidates(s, R, opts);
+  for (int i = 0; i < int(c.size()) && i < cap && splits; ++i) splits[i] = c[i];
+  return int(c.size());
+}
+
+cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
+                            const cpg_opts* opts, int reps, cpg_als_plan* chosen) {
+  Shape s;
+  cpg_status st = common_checks(opts, s, I, N, R);
+  if (st != CPG_OK) return st;
+  if (Y == nullptr || !ptrs_ok(const_cast<const void* const*>(A), N) || lambda == nullptr || reps < 1 || reps > 1000)
+    return CPG_ERR_ARG;
+  if (!sweep_prec_ok(opts->precision)) return CPG_ERR_UNSUPPORTED;
+  if (R > kAlsMaxRank) return CPG_ERR_UNSUPPORTED;
+  const int prec = opts->precision;
+  const std::vector<int> cand = als_candidates(s, R, opts);
+  size_t als_need = 0;
+  for (int k : cand) als_need = std::max(als_need, als_bytes(s, R, prec, k, true));
+  const size_t save_off = als_tune_save_offset(als_need);
+  if (opts->workspace == nullptr || opts->workspace_bytes < save_off + als_tune_save_bytes(s, R, prec))
+    return CPG_ERR_WORKSPACE;
+  cudaStream_t str = static_cast<cudaStream_t>(opts->stream);
+  const size_t es = is_f64(prec) ? 8 : 4;
+  unsigned char* save = static_cast<unsigned char*>(opts->workspace) + save_off;
+  // Copies between the caller's factors and lambda and the save area.
+  auto copy_all = [&](bool to_save) {
+    size_t off = 0;
+    for (int n = 0; n < N && st == CPG_OK; ++n) {
+      const size_t b = size_t(s.I[n]) * size_t(R) * es;
+      void* dst = to_save ? static_cast<void*>(save + off) : A[n];
+      const void* src = to_save ? static_cast<const void*>(A[n]) : static_cast<const void*>(save + off);
+      if (cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, str) != cudaSuccess) st = CPG_ERR_CUDA;
+      off += b;
+    }
+    off = align_up(off);
+    void* dl = to_save ? static_cast<void*>(save + off) : static_cast<void*>(lambda);
+    const void* sl = to_save ? static_cast<const void*>(lambda) : static_cast<const void*>(save + off);
+    if (st == CPG_OK && cudaMemcpyAsync(dl, sl, size_t(R) * sizeof(double), cudaMemcpyDeviceToDevice, str) != cudaSuccess)
+      st = CPG_ERR_CUDA;
+  };
+  cpg_opts o = *opts;
+  o.workspace_bytes = save_off;  // the sweeps never touch the save area
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CPG_ERR_CUDA;
+  auto run = [&](int iters) {
+    return is_f64(prec) ? als_impl<double>(s, static_cast<const double*>(Y), A, lambda, R, iters, nullptr, &o)
+                        : als_impl<float>(s, static_cast<const float*>(Y), A, lambda, R, iters, nullptr, &o);
+  };
+  copy_all(true);
+  int best = 0;
+  float best_ms = 0.f;
+  for (int k : cand) {
+    if (st != CPG_OK) break;
+    o.split = k;
+    st = run(1);  // untimed: planning, attribute setup and warm caches
+    copy_all(false);
+    if (st == CPG_OK && cudaEventRecord(e0, str) != cudaSuccess) st = CPG_ERR_CUDA;
+    if (st == CPG_OK) st = run(reps);
+    if (st == CPG_OK && (cudaEventRecord(e1, str) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      st = CPG_ERR_CUDA;
+    copy_all(false);
+    if (st != CPG_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= float(reps);
+    if (best == 0 || ms < best_ms) {
+      best = k;
+      best_ms = ms;
+    }
+  }
+  if (cudaStreamSynchronize(str) != cudaSuccess && st == CPG_OK) st = CPG_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != CPG_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tuned_mu);
+    g_als_tuned[tune_key(s, R, opts)] = best;
+  }
+  if (chosen) {
+    chosen->split = best;
+    chosen->ms = best_ms;
+    chosen->candidates = int(cand.size());
+  }
+  return CPG_OK;
+}
+
+int cpg_als_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_als_plan* plan) {
+  Shape s;
+  if (opts == nullptr || check_shape(I, N, R, s) != CPG_OK) return 0;
+  int k = 0;
+  if (!tuned_als_split(s, R, opts, &k)) return 0;
+  if (plan) {
+    plan->split = k;
+    plan->ms = 0.f;
+    plan->candidates = 0;
+  }
+  return 1;
 }
 
 cpg_status cp_gradient_mode(const void* Y, const int64_t* I, int N, const void* const* A, int R, int n, void* Gn,

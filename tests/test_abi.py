@@ -199,6 +199,47 @@ def test_autotune_arguments_and_sizes(L):
     assert cpgrad.gradient_plan([100] * 4, 10) is None
 
 
+def test_als_autotune_candidates_and_sizes(L):
+    """The CP_ALS autotuner's candidate splits, workspace and argument checks.
+    The cost model ranks splits by the partial results of Algorithm 2's
+    recursions; on the paper's cubical shapes n* (Algorithm 2 step 1) is
+    always a candidate and a split that puts all but one mode on one side
+    is not, once its partial result is as large as Y."""
+    for I_, R in (([100] * 4, 10), ([60] * 5, 32), ([60] * 5, 64), ([15] * 7, 10), ([30, 40, 50], 5)):
+        c = cpgrad.als_candidates(I_, R)
+        assert oracle.split_point(I_) in c
+        assert len(set(c)) == len(c) and all(1 <= k <= len(I_) - 1 for k in c)
+    # 60^5: splits 1 and 4 carry a partial result of 60^4 x R, about R/60 of Y
+    # twice over, far above the 1.25x margin; 2 and 3 cost the same
+    assert cpgrad.als_candidates([60] * 5, 32) == [2, 3]
+    # a requested split is the only candidate; a split out of range is an error
+    assert cpgrad.als_candidates([60] * 5, 32, split=4) == [4]
+    with pytest.raises(cpgrad.CpgError):
+        cpgrad.als_candidates([60] * 5, 32, split=5)
+    for I_, R in (([100] * 4, 10), ([60] * 5, 32), ([24, 20, 30, 17], 12)):
+        for prec in ("fp32", "bf16x6", "tf32x3"):
+            tune = cpgrad.cpg_workspace_size(I_, R, prec, 0, cpgrad.CALL_ALS_TUNE)
+            als = cpgrad.cpg_workspace_size(I_, R, prec, 0, cpgrad.CALL_ALS)
+            save = sum(I_) * R * 4 + R * 8
+            assert tune >= als + save, (I_, R, prec)
+    I = cpgrad._i64([4, 5, 6])
+    dummy = ctypes.c_void_p(16)
+    A = (ctypes.c_void_p * 3)(dummy, dummy, dummy)
+    o = _opts()
+    plan = cpgrad.cpg_als_plan()
+    n0 = cpgrad.launch_count(reset=True)
+    assert L.cpg_autotune_als(None, I, 3, A, dummy, 3, ctypes.byref(o), 2, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_als(dummy, I, 3, A, None, 3, ctypes.byref(o), 2, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_als(dummy, I, 3, A, dummy, 3, ctypes.byref(o), 0, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    assert L.cpg_autotune_als(dummy, I, 3, A, dummy, 3, None, 2, ctypes.byref(plan)) == cpgrad.CPG_ERR_ARG
+    ob = _opts(prec=cpgrad.PRECISIONS["bf16x3"])
+    assert L.cpg_autotune_als(dummy, I, 3, A, dummy, 3, ctypes.byref(ob), 2, None) == cpgrad.CPG_ERR_UNSUPPORTED
+    assert L.cpg_autotune_als(dummy, I, 3, A, dummy, 3, ctypes.byref(o), 2, None) == cpgrad.CPG_ERR_WORKSPACE
+    assert cpgrad.launch_count() == 0 * n0
+    cpgrad.autotune_clear()
+    assert cpgrad.als_plan([100] * 4, 10) is None
+
+
 def test_consumer_entry_points_check_arguments(L):
     """cp_gradient_full / cp_gradient_step / cp_ntf_iter return argument and
     workspace errors before launching anything."""
