@@ -79,6 +79,11 @@ struct TcArgs {
   const float* Y;  // the tensor (element loads when use_tma == 0)
   int64_t ldy;     // elements from one column of Y_(1:k) to the next (>= J)
   int use_tma;     // 1: TMA boxes; 0: element loads (rows not 16-byte aligned)
+  // Split-BF16 kernel: the Khatri-Rao B tiles of the pass, prebuilt in their
+  // shared-memory layout (ws_wimg_kernel), tile t at t * (tile bytes + 64):
+  // W_R tiles of KWR contraction entries (columns of Y), W_L of KWL (rows).
+  unsigned char* wimg_r;
+  unsigned char* wimg_l;
 };
 
 // 4-byte copy global -> shared with zero fill (src_bytes = 0 writes zeros and
@@ -110,10 +115,11 @@ struct WsCfg {
   static constexpr int NW = L * RTP;                // B rows, slot columns
   static constexpr uint32_t WR_BYTES = DO_R ? uint32_t(NW) * KWR * 2 : 0;
   static constexpr uint32_t WL_BYTES = DO_L ? uint32_t(NW) * KWL * 2 : 0;
-  // Warps: producer, MMA, 4 promotion, CW converters.
+  // Prebuilt B tiles in global memory: the limbs, then RTP exponent bytes
+  // (padded to 64).
+  static constexpr uint32_t WIMG_R_STRIDE = WR_BYTES + 64, WIMG_L_STRIDE = WL_BYTES + 64;
+  // Converter warps.
   static constexpr int CW = 8;
-  static constexpr int NWARP = 2 + 4 + CW;
-  static constexpr int NT = NWARP * 32;
   static constexpr int CT = CW * 32;                // converter threads
   static constexpr int OPT = 1024 / CT;             // octets (8 rows of a column) per thread per box
   // Fused pass: the W_L tiles of every row tile of the J-block stay in shared
@@ -146,6 +152,13 @@ struct WsCfg {
   // waiter: the MMAs of stage ss + NL need the converters' stage ss + NL and
   // the promotion's release of slot ss.
   static constexpr bool ONE_COMMIT = NSIDE == 1 && NL == NSLOT;
+  // MMA-issuing warps: with two limb stages and two slots, a second issuer
+  // takes the odd stages, so that one issuer's waits and bookkeeping overlap
+  // the other's MMAs in the tensor pipe.
+  static constexpr int NISS = (NL == 2 && NSLOT == 2) ? 2 : 1;
+  // Warps: producer, MMA issuer 0, 4 promotion, CW converters, MMA issuer 1.
+  static constexpr int NWARP = 2 + 4 + CW + (NISS - 1);
+  static constexpr int NT = NWARP * 32;
   static constexpr int NEXP = 8;                    // ring of per-tile scale exponents
 };
 
@@ -193,6 +206,67 @@ __device__ __forceinline__ void ws_split8(const float (&x)[8], uint4 (&out)[L]) 
   for (int q = 0; q < 4; ++q) ws_split_pair<L>(x[2 * q], x[2 * q + 1], p[q]);
 #pragma unroll
   for (int l = 0; l < L; ++l) out[l] = make_uint4(p[0][l], p[1][l], p[2][l], p[3][l]);
+}
+
+// One Khatri-Rao B tile: rank columns r0 .. r0 + RTP - 1 of `kr` over
+// contraction indices [base, base + KW) (zero past `limit` and past rank R),
+// each column scaled by 2^-e (e = floor(log2) of the column's largest
+// magnitude in the tile, so the scaling is exact), split into L BF16 limbs
+// and stored in the K-major swizzled layout of ws_boff; exps[r] = e.  Thread
+// t of nth (a multiple of 32) takes tasks of 8 consecutive indices of one
+// rank; the KW / 8 tasks of a rank are adjacent lanes of one warp.
+template <int RTP, int L, int KW>
+__device__ __forceinline__ void ws_build_w(unsigned char* tile, signed char* exps, const KrRows<float>& kr,
+                                           int64_t base, int64_t limit, int r0, int R, int t, int nth) {
+  constexpr int KWO = KW / 8;
+  const int lane = t & 31;
+  for (int t0 = t & ~31; t0 < RTP * KWO; t0 += nth) {
+    const int task = t0 + lane;
+    const int r = task / KWO, ko = task % KWO;
+    const bool rok = r0 + r < R;
+    float w[8];
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t g = base + ko * 8 + e;
+      w[e] = (rok && g < limit) ? kr.at(uint32_t(g), r0 + r) : 0.f;
+      m = fmaxf(m, fabsf(w[e]));
+    }
+#pragma unroll
+    for (int o = KWO / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int ex = 0;
+    if (m > 0.f) {
+      ex = int((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) for normal m
+      ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+    }
+    const float sc = __int_as_float((127 - ex) << 23);  // 2^-ex
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w[e] *= sc;
+    uint4 limbs[L];
+    ws_split8<L>(w, limbs);
+#pragma unroll
+    for (int l = 0; l < L; ++l) *reinterpret_cast<uint4*>(tile + ws_boff<KW>(l * RTP + r, ko * 8)) = limbs[l];
+    if (ko == 0) exps[r] = static_cast<signed char>(ex);
+  }
+}
+
+// The B tiles of one pass, built once in global memory (where the leading
+// kernel's producer copies them from with one bulk copy each): tile t covers
+// contraction indices [t KW, (t + 1) KW), zero from `limit` on.  A CTA's
+// column range starts and ends on tile boundaries (or at K), so these are
+// the tiles the CTAs would build for themselves.  grid-stride over tiles,
+// 256 threads.
+template <int RTP, int L, int KW>
+__global__ void __launch_bounds__(256) ws_wimg_kernel(unsigned char* img, const KrRows<float> kr, int64_t limit,
+                                                      int r0, int R, int64_t ntiles) {
+  griddep_wait();
+  constexpr uint32_t WB = uint32_t(L * RTP) * KW * 2, STRIDE = WB + 64;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    unsigned char* tile = img + t * STRIDE;
+    ws_build_w<RTP, L, KW>(tile, reinterpret_cast<signed char*>(tile + WB), kr, t * KW, limit, r0, R, threadIdx.x,
+                           256);
+  }
+  griddep_launch();
 }
 
 __device__ __forceinline__ uint64_t ws_globaltimer() {
@@ -288,11 +362,11 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
     }
     for (int i = 0; i < WBR; ++i) {
       tc::mbar_init(&wr_full[i], C::CW);
-      tc::mbar_init(&wr_empty[i], 1);
+      tc::mbar_init(&wr_empty[i], C::NISS);
     }
     for (int i = 0; i < (WBL > 0 ? WBL : 1); ++i) {
       tc::mbar_init(&wl_full[i], C::CW);
-      tc::mbar_init(&wl_empty[i], 1);
+      tc::mbar_init(&wl_empty[i], C::NISS);
     }
     for (int i = 0; i < NEXP; ++i) {
       tc::mbar_init(&exr_full[i], C::CW);
@@ -303,7 +377,7 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
         tc::mbar_init(&slot_full[s][i], 1);
         tc::mbar_init(&slot_empty[s][i], 4);
       }
-    tc::mbar_init(&mma_done, 1);
+    tc::mbar_init(&mma_done, C::NISS);
     tc::mbar_fence_init();
     abort_flag = 0;
   }
@@ -347,9 +421,15 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
           tc::mbar_wait(&raw_full[u % NRU], uint32_t(u / NRU) & 1u, 1u << 16);
       }
     }
-  } else if (warp == 1) {
-    // ---- MMA issuer -----------------------------------------------------------------
+  } else if (warp == 1 || (C::NISS == 2 && warp == 6 + C::CW)) {
+    // ---- MMA issuers ----------------------------------------------------------------
+    // Issuer p takes stages p, p + NISS, ...  Each tcgen05.commit tracks the
+    // MMAs of its own thread, so a B tile that both issuers read is released
+    // by one commit of each (a chunk or row tile with a single stage gets
+    // both commits from the issuer that has it).
     if (lane == 0) {
+      constexpr int NISS = C::NISS;
+      const int p = warp == 1 ? 0 : 1;
       // This one thread bounds the pass when its loop is long (a stage's MMAs
       // wait for its scalar work), so the loop is kept short: the stage
       // coordinates advance by counters, and every shared-memory descriptor is
@@ -362,8 +442,8 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
       const uint64_t b_r0 = tc::smem_desc_sw128(tc::smem_addr(sm + C::OFF_WR), 16, (C::KWR / 64) * 1024);
       const uint64_t b_l0 = tc::smem_desc_sw128(tc::smem_addr(sm + C::OFF_WL), 16, (C::KWL / 64) * 1024);
       const uint32_t dslot = tbase + slot0;
-      int q = 0, rt = 0;  // chunk and row tile of stage ss
-      for (int ss = 0; ss < nss; ++ss) {
+      int q = chunk_of(p), rt = tile_of(p);  // chunk and row tile of stage ss
+      for (int ss = p; ss < nss; ss += NISS) {
         const int ls = ss % NL, sl = ss % NSLOT;
         if constexpr (DO_R) {
           if (!ws_wait(&wr_full[q % WBR], uint32_t(q / WBR) & 1u, abort)) break;
@@ -413,22 +493,31 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
         tc::mma_commit(&limb_empty[ls]);
         if constexpr (!C::ONE_COMMIT)
           for (int s = 0; s < C::NSIDE; ++s) tc::mma_commit(&slot_full[s][sl]);
-        if constexpr (DO_R) {
-          if (rt == nrt - 1) tc::mma_commit(&wr_empty[q % WBR]);
-        }
-        if constexpr (SIDES == 2) {
-          if (q == nchunk - 1) tc::mma_commit(&wl_empty[rt % WBL]);
-        }
-        // next stage's coordinates (the loop order of chunk_of / tile_of)
-        if constexpr (ROWS_OUTER) {
-          if (++q == nchunk) {
-            q = 0;
-            ++rt;
+        if constexpr (DO_R) {  // this issuer's last stage of chunk q
+          if (rt + NISS >= nrt) {
+            tc::mma_commit(&wr_empty[q % WBR]);
+            if (NISS == 2 && nrt == 1) tc::mma_commit(&wr_empty[q % WBR]);
           }
-        } else {
-          if (++rt == nrt) {
-            rt = 0;
-            ++q;
+        }
+        if constexpr (SIDES == 2) {  // this issuer's last stage of row tile rt
+          if (q + NISS >= nchunk) {
+            tc::mma_commit(&wl_empty[rt % WBL]);
+            if (NISS == 2 && nchunk == 1) tc::mma_commit(&wl_empty[rt % WBL]);
+          }
+        }
+        // this issuer's next stage (the loop order of chunk_of / tile_of)
+#pragma unroll
+        for (int i = 0; i < NISS; ++i) {
+          if constexpr (ROWS_OUTER) {
+            if (++q == nchunk) {
+              q = 0;
+              ++rt;
+            }
+          } else {
+            if (++rt == nrt) {
+              rt = 0;
+              ++q;
+            }
           }
         }
       }
@@ -531,7 +620,7 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
         }
       }
     }
-  } else {
+  } else if (warp < 6 + C::CW) {
     // ---- converters -------------------------------------------------------------------
     const int ct = tid - 6 * 32, cw = ct >> 5;
     float ysq = 0.f;
