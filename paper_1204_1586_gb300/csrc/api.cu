@@ -304,6 +304,11 @@ LeadPlan plan_lead_tc(const Shape& s, int R, int k, int sides, int prec) {
   }
   p.rpart_elems = (sides & 1) ? size_t(p.nKs) * R * p.J : 0;
   p.lpart_elems = (sides & 2) ? size_t(p.nJb) * R * p.K : 0;
+  // Prebuilt B tiles of the split-BF16 passes (in the W row tables' place).
+  size_t rb = 0, lb = 0;
+  tc_wimg_bytes(p.RTP, sides, p.tc_prec, p.J, p.K, p.nrt, &rb, &lb);
+  p.wr_elems = (rb + 3) / 4;
+  p.wl_elems = (lb + 3) / 4;
   return p;
 }
 
@@ -633,11 +638,19 @@ cudaError_t run_lead(const Shape& s, const T* Y, const void* const* A, int R, co
       a.Rpart = Rpart;
       a.Lpart = Lpart;
       a.status = g_status_ptr;
+      a.wimg_r = reinterpret_cast<unsigned char*>(tabs.wR);
+      a.wimg_l = reinterpret_cast<unsigned char*>(tabs.wL);
       for (int g = 0; g < p.groups; ++g) {
         a.r0 = g * p.RTmax;
         a.normpart = (g == 0) ? normpart : nullptr;
-        ++g_launches;
         cudaError_t e;
+        if (p.wr_elems + p.wl_elems > 0) {
+          g_launches += ((p.sides & 1) ? 1 : 0) + ((p.sides & 2) ? 1 : 0);
+          Timed timer(st, kKindRows);
+          e = launch_lead_tc_prep(a, p.RTP, p.sides, p.tc_prec, num_sms(), st);
+          if (e != cudaSuccess) return e;
+        }
+        ++g_launches;
         {
           Timed timer(st, p.sides);
           e = launch_lead_tc(Y, a, p.RTP, p.sides, p.tc_prec, dim3(p.nJb, p.nKs), st);

@@ -62,6 +62,48 @@ int tc_fused_max_nrt(int RTP, int prec) {
   return std::min(nwlc, tc_max_acc(RTP, 3, prec) - 1);
 }
 
+namespace {
+
+template <int SIDES, int L>
+void wimg_bytes_rtp(int RTP, int64_t J, int64_t K, int nrt, size_t* rb, size_t* lb) {
+  if (RTP <= 16) return wimg_bytes<16, SIDES, L>(J, K, nrt, rb, lb);
+  if (RTP <= 32) return wimg_bytes<32, SIDES, L>(J, K, nrt, rb, lb);
+  if constexpr (SIDES != 3) return wimg_bytes<64, SIDES, L>(J, K, nrt, rb, lb);
+}
+
+template <int SIDES>
+void wimg_bytes_l(int RTP, int L, int64_t J, int64_t K, int nrt, size_t* rb, size_t* lb) {
+  if (L == 1) return wimg_bytes_rtp<SIDES, 1>(RTP, J, K, nrt, rb, lb);
+  if (L == 2) return wimg_bytes_rtp<SIDES, 2>(RTP, J, K, nrt, rb, lb);
+  if constexpr (SIDES != 3) return wimg_bytes_rtp<SIDES, 3>(RTP, J, K, nrt, rb, lb);
+}
+
+}  // namespace
+
+void tc_wimg_bytes(int RTP, int sides, int prec, int64_t J, int64_t K, int nrt, size_t* rb, size_t* lb) {
+  *rb = 0;
+  *lb = 0;
+  if (prec == kTcTf32x3) return;
+  const int L = limbs_of(prec);
+  switch (sides) {
+    case 1: return wimg_bytes_l<1>(RTP, L, J, K, nrt, rb, lb);
+    case 2: return wimg_bytes_l<2>(RTP, L, J, K, nrt, rb, lb);
+    case 3: return wimg_bytes_l<3>(RTP, L, J, K, nrt, rb, lb);
+    default: return;
+  }
+}
+
+cudaError_t launch_lead_tc_prep(const TcArgs& a, int RTP, int sides, int prec, int nsm, cudaStream_t st) {
+  if (prec == kTcTf32x3) return cudaSuccess;
+  const int L = limbs_of(prec);
+  switch (sides) {
+    case 1: return prep_ws_sides1(a, RTP, L, nsm, st);
+    case 2: return prep_ws_sides2(a, RTP, L, nsm, st);
+    case 3: return prep_ws_sides3(a, RTP, L, nsm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st) {
   if (prec == kTcTf32x3) return launch_lead_tf32(Y, a, RTP, sides, grid, st);
   CUtensorMap m{};

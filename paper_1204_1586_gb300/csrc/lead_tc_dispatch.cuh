@@ -25,6 +25,12 @@ int tc_max_acc(int RTP, int sides, int prec);
 // tiles per J-block it can keep the step-7 Khatri-Rao tiles of.
 bool tc_fused_ok(int RTP, int prec);
 int tc_fused_max_nrt(int RTP, int prec);
+// Split-BF16 passes: bytes of the prebuilt Khatri-Rao B tiles (R side, L
+// side, for J-blocks of nrt row tiles; 0 for TF32x3) and the launches that
+// build them (a.wimg_r / a.wimg_l,
+// from a.wr / a.wl for ranks a.r0 ..) ahead of the pass.
+void tc_wimg_bytes(int RTP, int sides, int prec, int64_t J, int64_t K, int nrt, size_t* rb, size_t* lb);
+cudaError_t launch_lead_tc_prep(const TcArgs& a, int RTP, int sides, int prec, int nsm, cudaStream_t st);
 // TMA needs a 16-byte aligned tensor and rows of whole 16-byte chunks; other
 // tensors are read with element loads.
 cudaError_t launch_lead_tc(const float* Y, const TcArgs& a, int RTP, int sides, int prec, dim3 grid, cudaStream_t st);

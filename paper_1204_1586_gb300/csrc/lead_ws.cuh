@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
   __shared__ uint64_t exr_full[NEXP], exl_full[NEXP];
   __shared__ uint64_t slot_full[C::NSIDE][NSLOT], slot_empty[C::NSIDE][NSLOT];
   __shared__ uint64_t mma_done;
-  __shared__ signed char expR[NEXP][RTP];
-  __shared__ signed char expL[(SIDES == 3 ? C::NWLC : NEXP)][RTP];
+  __shared__ __align__(16) signed char expR[NEXP][RTP];
+  __shared__ __align__(16) signed char expL[(SIDES == 3 ? C::NWLC : NEXP)][RTP];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   __shared__ double wsum[C::CW];
@@ -360,17 +360,18 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
       tc::mbar_init(&limb_full[i], C::CW);
       tc::mbar_init(&limb_empty[i], 1);
     }
+    // B tiles and their exponents arrive by the producer's bulk copies.
     for (int i = 0; i < WBR; ++i) {
-      tc::mbar_init(&wr_full[i], C::CW);
+      tc::mbar_init(&wr_full[i], 1);
       tc::mbar_init(&wr_empty[i], C::NISS);
     }
     for (int i = 0; i < (WBL > 0 ? WBL : 1); ++i) {
-      tc::mbar_init(&wl_full[i], C::CW);
+      tc::mbar_init(&wl_full[i], 1);
       tc::mbar_init(&wl_empty[i], C::NISS);
     }
     for (int i = 0; i < NEXP; ++i) {
-      tc::mbar_init(&exr_full[i], C::CW);
-      tc::mbar_init(&exl_full[i], C::CW);
+      tc::mbar_init(&exr_full[i], 1);
+      tc::mbar_init(&exl_full[i], 1);
     }
     for (int s = 0; s < C::NSIDE; ++s)
       for (int i = 0; i < NSLOT; ++i) {
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tslot;
-  const bool bad_shape = nacc > C::MAX_ACC || (SIDES == 3 && nrt > C::NWLC);
+  const bool bad_shape = nacc > C::MAX_ACC || (SIDES == 3 && nrt > C::NWLC) || (DO_R && a.wimg_r == nullptr) ||
+                         (DO_L && a.wimg_l == nullptr);
 
   // ---- TMA producer ------------------------------------------------------------------
   // Unit u = box (u % UNITS) of stage u / UNITS.
@@ -410,15 +412,78 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
   if (bad_shape) {
     if (tid == 0) abort_flag = 1;
   } else if (warp == 0) {
-    if (lane == 0 && use_tma) {
-      for (; issued < nunits; ++issued) {
-        const int slot = issued % NRU;
-        if (!ws_wait(&raw_empty[slot], uint32_t(issued / NRU - 1) & 1u, abort)) break;
-        issue_unit(issued);
+    if (lane == 0) {
+      // In stage order: the stage's B tiles (W_R at the first row tile of a
+      // chunk, W_L at the first chunk of a row tile; fused: every row tile's
+      // W_L during the first chunk, kept), each a bulk copy of the prebuilt
+      // limbs plus one of its exponents, then the stage's boxes of Y.
+      int nwr = 0, nwl = 0;  // B tiles copied
+      auto copy_w = [&](uint64_t* full, uint64_t* exfull, unsigned char* dst, signed char* edst,
+                        const unsigned char* src, uint32_t bytes) {
+        tc::mbar_arrive_expect_tx(full, bytes);
+        tc::bulk_load(dst, src, bytes, full);
+        tc::mbar_arrive_expect_tx(exfull, uint32_t(RTP));
+        tc::bulk_load(edst, src + bytes, uint32_t(RTP), exfull);
+      };
+      for (int ss = 0; ss < nss; ++ss) {
+        const int q = chunk_of(ss), rt = tile_of(ss);
+        bool ok = true;
+        if constexpr (DO_R) {
+          if (rt == 0) {
+            if (q >= WBR) ok = ws_wait(&wr_empty[q % WBR], uint32_t(q / WBR - 1) & 1u, abort);
+            if (ok) {
+              copy_w(&wr_full[q % WBR], &exr_full[q % NEXP], sm + C::OFF_WR + (q % WBR) * C::WR_BYTES, expR[q % NEXP],
+                     a.wimg_r + (kbeg / SC + q) * int64_t(C::WIMG_R_STRIDE), C::WR_BYTES);
+              ++nwr;
+            }
+          }
+        }
+        if constexpr (SIDES == 2) {
+          if (ok && q == 0) {
+            if (rt >= WBL) ok = ws_wait(&wl_empty[rt % WBL], uint32_t(rt / WBL - 1) & 1u, abort);
+            if (ok) {
+              copy_w(&wl_full[rt % WBL], &exl_full[rt % NEXP], sm + C::OFF_WL + (rt % WBL) * C::WL_BYTES,
+                     expL[rt % NEXP], a.wimg_l + (jblk / SR + rt) * int64_t(C::WIMG_L_STRIDE), C::WL_BYTES);
+              ++nwl;
+            }
+          }
+        } else if constexpr (SIDES == 3) {
+          if (q == 0) {
+            copy_w(&wl_full[rt], &exl_full[rt], sm + C::OFF_WL + rt * C::WL_BYTES, expL[rt],
+                   a.wimg_l + (jblk / SR + rt) * int64_t(C::WIMG_L_STRIDE), C::WL_BYTES);
+            ++nwl;
+          }
+        }
+        if (ok && use_tma) {
+          for (int h = 0; h < UNITS && ok; ++h) {
+            const int u = ss * UNITS + h;
+            if (u < issued) continue;
+            const int slot = u % NRU;
+            if (u >= NRU) ok = ws_wait(&raw_empty[slot], uint32_t(u / NRU - 1) & 1u, abort);
+            if (ok) {
+              issue_unit(u);
+              issued = u + 1;
+            }
+          }
+        }
+        if (!ok) break;
       }
       if (*abort) {  // let this CTA's own copies land before its memory is released
         for (int u = (issued > NRU ? issued - NRU : 0); u < issued; ++u)
           tc::mbar_wait(&raw_full[u % NRU], uint32_t(u / NRU) & 1u, 1u << 16);
+        if constexpr (DO_R) {
+          for (int i = (nwr > WBR ? nwr - WBR : 0); i < nwr; ++i)
+            tc::mbar_wait(&wr_full[i % WBR], uint32_t(i / WBR) & 1u, 1u << 16);
+          for (int i = (nwr > NEXP ? nwr - NEXP : 0); i < nwr; ++i)
+            tc::mbar_wait(&exr_full[i % NEXP], uint32_t(i / NEXP) & 1u, 1u << 16);
+        }
+        if constexpr (DO_L) {
+          constexpr int NB = SIDES == 3 ? C::NWLC : WBL, NE = SIDES == 3 ? C::NWLC : NEXP;
+          for (int i = (nwl > NB ? nwl - NB : 0); i < nwl; ++i)
+            tc::mbar_wait(&wl_full[i % NB], uint32_t(i / NB) & 1u, 1u << 16);
+          for (int i = (nwl > NE ? nwl - NE : 0); i < nwl; ++i)
+            tc::mbar_wait(&exl_full[i % NE], uint32_t(i / NE) & 1u, 1u << 16);
+        }
       }
     }
   } else if (warp == 1 || (C::NISS == 2 && warp == 6 + C::CW)) {
@@ -625,81 +690,9 @@ __global__ void __launch_bounds__(WsCfg<RTP, SIDES, L>::NT, 1)
     const int ct = tid - 6 * 32, cw = ct >> 5;
     float ysq = 0.f;
     const bool do_norm = DO_R && a.normpart != nullptr;
-    // One Khatri-Rao B tile: rank columns r0 .. r0 + RTP - 1 over contraction
-    // indices [base, base + KW) (zero past `limit` and past rank R), each
-    // column scaled by 2^-e (e from the column's largest entry in the tile),
-    // split into L limbs.  A task is 8 consecutive indices of one rank; the
-    // KW / 8 tasks of a rank are adjacent lanes of one warp.
-    auto build_w = [&](unsigned char* tile, signed char* exps, const KrRows<float>& kr, int64_t base, int64_t limit,
-                       auto kw_tag) {
-      constexpr int KW = decltype(kw_tag)::value;
-      constexpr int KWO = KW / 8;
-      for (int t0 = cw * 32; t0 < RTP * KWO; t0 += C::CT) {
-        const int task = t0 + lane;
-        const int r = task / KWO, ko = task % KWO;
-        const bool rok = r0 + r < R;
-        float w[8];
-        float m = 0.f;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int64_t g = base + ko * 8 + e;
-          w[e] = (rok && g < limit) ? kr.at(uint32_t(g), r0 + r) : 0.f;
-          m = fmaxf(m, fabsf(w[e]));
-        }
-#pragma unroll
-        for (int o = KWO / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        int ex = 0;
-        if (m > 0.f) {
-          ex = int((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) for normal m
-          ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
-        }
-        const float s = ws_pow2(-ex);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) w[e] *= s;
-        uint4 limbs[L];
-        ws_split8<L>(w, limbs);
-#pragma unroll
-        for (int l = 0; l < L; ++l) *reinterpret_cast<uint4*>(tile + ws_boff<KW>(l * RTP + r, ko * 8)) = limbs[l];
-        if (ko == 0) exps[r] = static_cast<signed char>(ex);
-      }
-      tc::fence_async_smem();
-      __syncwarp();
-    };
-    using KwR = std::integral_constant<int, C::KWR>;
-    using KwL = std::integral_constant<int, C::KWL>;
     for (int ss = 0; ss < nss; ++ss) {
       const int q = chunk_of(ss), rt = tile_of(ss);
       const int64_t c0 = kbeg + int64_t(q) * SC, j0 = jblk + int64_t(rt) * SR;
-      // Khatri-Rao B tiles: W_R at the first row tile of a chunk, W_L at the
-      // first chunk of a row tile (fused: once per row tile, kept).
-      if constexpr (DO_R) {
-        if (rt == 0) {
-          if (q >= WBR && !ws_wait(&wr_empty[q % WBR], uint32_t(q / WBR - 1) & 1u, abort)) break;
-          build_w(sm + C::OFF_WR + (q % WBR) * C::WR_BYTES, expR[q % NEXP], a.wr, c0, kend, KwR{});
-          if (lane == 0) {
-            tc::mbar_arrive(&wr_full[q % WBR]);
-            tc::mbar_arrive(&exr_full[q % NEXP]);
-          }
-        }
-      }
-      if constexpr (SIDES == 2) {
-        if (q == 0) {
-          if (rt >= WBL && !ws_wait(&wl_empty[rt % WBL], uint32_t(rt / WBL - 1) & 1u, abort)) break;
-          build_w(sm + C::OFF_WL + (rt % WBL) * C::WL_BYTES, expL[rt % NEXP], a.wl, j0, J, KwL{});
-          if (lane == 0) {
-            tc::mbar_arrive(&wl_full[rt % WBL]);
-            tc::mbar_arrive(&exl_full[rt % NEXP]);
-          }
-        }
-      } else if constexpr (SIDES == 3) {
-        if (q == 0) {
-          build_w(sm + C::OFF_WL + rt * C::WL_BYTES, expL[rt], a.wl, j0, J, KwL{});
-          if (lane == 0) {
-            tc::mbar_arrive(&wl_full[rt]);
-            tc::mbar_arrive(&exl_full[rt]);
-          }
-        }
-      }
       // The stage's FP32 values: octet o of box h is column o / (RU / 8),
       // rows 8 (o % (RU / 8)) .. + 7 of the box.
       float x[UNITS][C::OPT][8];

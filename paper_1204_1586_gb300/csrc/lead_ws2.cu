@@ -12,4 +12,13 @@ cudaError_t launch_ws_sides2(const CUtensorMap& m, const TcArgs& a, int RTP, int
   }
 }
 
+cudaError_t prep_ws_sides2(const TcArgs& a, int RTP, int L, int nsm, cudaStream_t st) {
+  switch (L) {
+    case 1: return prep_ws_rtp<2, 1>(a, RTP, nsm, st);
+    case 2: return prep_ws_rtp<2, 2>(a, RTP, nsm, st);
+    case 3: return prep_ws_rtp<2, 3>(a, RTP, nsm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace cpg
