@@ -58,7 +58,9 @@ bool tc_fused_ok(int RTP, int prec) { return prec != kTcTf32x3 && limbs_of(prec)
 
 int tc_fused_max_nrt(int RTP, int prec) {
   if (!tc_fused_ok(RTP, prec)) return 0;
-  const int nwlc = RTP <= 16 ? WsCfg<16, 3, 1>::NWLC : WsCfg<32, 3, 1>::NWLC;
+  const bool one = limbs_of(prec) == 1;
+  const int nwlc = RTP <= 16 ? (one ? WsCfg<16, 3, 1>::NWLC : WsCfg<16, 3, 2>::NWLC)
+                             : (one ? WsCfg<32, 3, 1>::NWLC : WsCfg<32, 3, 2>::NWLC);
   return std::min(nwlc, tc_max_acc(RTP, 3, prec) - 1);
 }
 
