@@ -3,7 +3,10 @@ workload, for a profiler to capture (e.g. ncu -k regex:lead_ -c 5):
 
   1-2  one FP32 CP_ALS sweep: lead_simt_kernel step 4, then step 7;
   3-4  one BF16x6 CP_ALS sweep: lead_ws_kernel step 4, then step 7;
-  5    one BF16x3 all-mode gradient: lead_ws_kernel, steps 4 and 7 fused.
+  5    one BF16x3 all-mode gradient: lead_ws_kernel, steps 4 and 7 fused;
+  6-7  one TF32x3 CP_ALS sweep: lead_tf32_kernel step 4, then step 7.
+The split-BF16 passes are each preceded by ws_wimg_kernel launches that
+build their Khatri-Rao tiles.
 
 The tensor is N(0,1) (400 MB, larger than L2); the factors are N(0,1).  Run
 from the repository root: python -m paper_1204_1586_gb300.profile_lead
@@ -23,9 +26,10 @@ def main() -> None:
     cg.cp_als_iter(Y, I, [a.clone() for a in A0], 1, precision="fp32", workspace=ws, split=2)
     cg.cp_als_iter(Y, I, [a.clone() for a in A0], 1, precision="bf16x6", workspace=ws, split=2)
     cg.cp_gradient_all(Y, I, A0, precision="bf16x3", workspace=ws, split=2)
+    cg.cp_als_iter(Y, I, [a.clone() for a in A0], 1, precision="tf32x3", workspace=ws, split=2)
     torch.cuda.synchronize()
     assert cg.cpg_device_status(workspace=ws) == 0
-    print("profile_lead: 5 leading launches done")
+    print("profile_lead: 7 leading launches done")
 
 
 if __name__ == "__main__":
