@@ -87,6 +87,8 @@ GRAD_CASES = [
     ([9, 10, 11], 70, "bf16x6"),        # J=9: element loads, two rank groups
     ([15, 15, 15, 15, 15], 10, "bf16x6"),  # J=225: element loads
     ([20, 12, 40, 36], 33, "bf16x6"),   # rank tile 64, R not a multiple of 16
+    ([10, 12, 14], 130, "bf16x6"),      # three rank groups: the B tiles rebuilt per group
+    ([16, 8, 24, 6], 200, "bf16x3"),    # four rank groups, the last of 8 ranks
     # split-TF32 products on the tensor cores (one side per pass; 128 x 64
     # step-4 tiles, 64 x 128 step-7 tiles)
     ([24, 20, 30, 17], 12, "tf32x3"),   # k=2, J=480: TMA boxes, ragged row tile and column chunk

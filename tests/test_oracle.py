@@ -12,7 +12,10 @@ none of which re-types the oracle's own unfold-and-multiply code.
   D (eq. 2.12) summed entry by entry, and zero at an exact factorisation; a
   small first-order step (eq. 2.15) lowers D by 2 eta ||G||^2 to first order;
 * multiplicative NTF (eq. 2.18): fixed point at an exact nonnegative
-  factorisation, non-increasing D, nonnegative factors, cheap fit = explicit.
+  factorisation, non-increasing D, nonnegative factors, cheap fit = explicit;
+* the normal-equation solve of eq. 2.14 with a singular V (two equal factor
+  columns): the result solves A V = G exactly when G is consistent and its
+  rows lie in the range of V, which together make it G V^dagger.
 """
 import itertools
 import json
@@ -147,6 +150,42 @@ def test_mode_order():
     assert oracle.als_mode_order([100] * 4) == [1, 0, 2, 3]
     assert oracle.als_mode_order([15] * 7) == [2, 1, 0, 3, 4, 5, 6]
     assert oracle.als_mode_order([30, 40, 50]) == [0, 1, 2]
+
+
+def test_solve_normal_singular_is_minimum_norm_solution():
+    """A singular V, as when two columns of a factor coincide, sends the
+    oracle's solve of eq. 2.14 to its eigen branch.  For G = X V (a
+    consistent system) the Moore-Penrose solution G V^dagger is the unique A
+    with A V = G whose rows lie in range(V): check both properties, plus a
+    rank-one V built from equal columns, without forming a pseudo-inverse."""
+    from oracle.cp_oracle import _solve_normal
+    g = cpsynth.rng(41)
+    R = 6
+    B = g.standard_normal((R, 4))
+    V = B @ B.T                                   # PSD, rank 4
+    with pytest.raises(np.linalg.LinAlgError):
+        np.linalg.cholesky(V)
+    X = g.standard_normal((9, R))
+    G = X @ V
+    A = _solve_normal(G, V)
+    assert np.linalg.norm(A @ V - G) <= 1e-10 * np.linalg.norm(G)
+    w, Q = np.linalg.eigh(V)
+    null = Q[:, w < 1e-9 * w.max()]               # basis of V's null space
+    assert null.shape[1] == 2
+    assert np.linalg.norm(A @ null) <= 1e-10 * np.linalg.norm(A)
+    # any other solution differs by a null-space term and is longer
+    other = A + g.standard_normal((9, 2)) @ null.T
+    assert np.linalg.norm(other @ V - G) <= 1e-10 * np.linalg.norm(G)
+    assert np.linalg.norm(other) > np.linalg.norm(A)
+    # equal columns: a^(m) columns 0 and 1 coincide in every other mode, so
+    # V = Hadamard of the other Grams has equal rows/columns 0 and 1
+    a = g.standard_normal((7, 3))
+    a[:, 1] = a[:, 0]
+    V2 = (a.T @ a) * (a.T @ a)
+    G2 = g.standard_normal((5, 3)) @ V2
+    A2 = _solve_normal(G2, V2)
+    assert np.linalg.norm(A2 @ V2 - G2) <= 1e-10 * np.linalg.norm(G2)
+    assert np.allclose(A2[:, 0], A2[:, 1], atol=1e-12 * np.abs(A2).max())  # no null-space component
 
 
 def test_als_eckart_young():
