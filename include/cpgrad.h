@@ -166,6 +166,15 @@ cpg_status cpg_autotune_gradient(const void* Y, const int64_t* I, int N, const v
  * rank and opts (precision, split, current device); 0 otherwise.  Host-only. */
 int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_gradient_plan* plan);
 
+/* Records *plan as the measured plan for this shape, rank and opts
+ * (precision, split, current device), as cpg_autotune_gradient would: a plan
+ * kept from an earlier run, or one a caller wants to pin.  Host-only.
+ * CPG_ERR_ARG for a split outside [1, N-1] (or other than a nonzero
+ * opts->split), CPG_ERR_UNSUPPORTED for a fused plan the precision has no
+ * fused pass for; shape errors as for cp_gradient_all. */
+cpg_status cpg_gradient_plan_set(const int64_t* I, int N, int R, const cpg_opts* opts,
+                                 const cpg_gradient_plan* plan);
+
 /* Forgets every recorded plan (gradient plans and CP_ALS splits). */
 void cpg_autotune_clear(void);
 
@@ -208,6 +217,11 @@ cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const*
  * shape, rank and opts (precision, split, current device); 0 otherwise.
  * Host-only. */
 int cpg_als_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts, cpg_als_plan* plan);
+
+/* Records plan->split as the measured CP_ALS split for this shape, rank and
+ * opts, as cpg_autotune_als would.  Host-only; errors as for
+ * cpg_gradient_plan_set. */
+cpg_status cpg_als_plan_set(const int64_t* I, int N, int R, const cpg_opts* opts, const cpg_als_plan* plan);
 
 /* Single-mode CP gradient, Section 3.2: G^(n) via the right-to-left route
  * (eqs. 3.7, 3.10, 3.12) when J_n <= K_{n-1}, else the left-to-right route

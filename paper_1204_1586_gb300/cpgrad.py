@@ -28,7 +28,8 @@ EXPORTS = ["cpg_split_point", "cpg_workspace_size", "cp_gradient_all", "cp_gradi
            "cpg_workspace_size_batched", "cp_als_batched", "cpg_workspace_init", "cpg_device_status", "cpg_status_str",
            "cpg_launch_count", "cpg_profile_lead", "cpg_profile_read", "cpg_autotune_gradient",
            "cpg_gradient_plan_query", "cpg_autotune_clear", "cp_gradient_full", "cp_gradient_step", "cp_ntf_iter",
-           "cpg_selftest_timeout", "cpg_als_candidates", "cpg_autotune_als", "cpg_als_plan_query"]
+           "cpg_selftest_timeout", "cpg_als_candidates", "cpg_autotune_als", "cpg_als_plan_query",
+           "cpg_gradient_plan_set", "cpg_als_plan_set"]
 
 
 class CpgError(RuntimeError):
@@ -116,6 +117,12 @@ def lib() -> ctypes.CDLL:
         L.cpg_als_plan_query.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
                                          ctypes.POINTER(cpg_als_plan)]
         L.cpg_als_plan_query.restype = ctypes.c_int
+        L.cpg_gradient_plan_set.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
+                                            ctypes.POINTER(cpg_gradient_plan)]
+        L.cpg_gradient_plan_set.restype = ctypes.c_int
+        L.cpg_als_plan_set.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(cpg_opts),
+                                       ctypes.POINTER(cpg_als_plan)]
+        L.cpg_als_plan_set.restype = ctypes.c_int
         L.cp_gradient_full.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int, vpp, ctypes.c_int, vpp,
                                        ctypes.POINTER(cpg_opts)]
         L.cp_gradient_full.restype = ctypes.c_int
@@ -378,6 +385,24 @@ def gradient_plan(I: Sequence[int], R: int, precision="fp32", split: int = 0):
     if not lib().cpg_gradient_plan_query(_i64(I), len(I), int(R), ctypes.byref(o), ctypes.byref(plan)):
         return None
     return {"split": plan.split, "fused": bool(plan.fused)}
+
+
+def set_gradient_plan(I: Sequence[int], R: int, split: int, fused: bool, precision="fp32") -> None:
+    """Records (split, fused) as the plan later cp_gradient_all calls of this shape / rank / precision run."""
+    o = cpg_opts(_prec(precision), 0, None, 0, None)
+    plan = cpg_gradient_plan(int(split), 1 if fused else 0, 0.0, 0)
+    st = lib().cpg_gradient_plan_set(_i64(I), len(I), int(R), ctypes.byref(o), ctypes.byref(plan))
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_gradient_plan_set")
+
+
+def set_als_plan(I: Sequence[int], R: int, split: int, precision="fp32") -> None:
+    """Records split as the CP_ALS split later sweeps of this shape / rank / precision run."""
+    o = cpg_opts(_prec(precision), 0, None, 0, None)
+    plan = cpg_als_plan(int(split), 0.0, 0)
+    st = lib().cpg_als_plan_set(_i64(I), len(I), int(R), ctypes.byref(o), ctypes.byref(plan))
+    if st != CPG_OK:
+        raise CpgError(st, "cpg_als_plan_set")
 
 
 def autotune_clear() -> None:

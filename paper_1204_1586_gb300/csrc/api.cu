@@ -1633,6 +1633,35 @@ int cpg_gradient_plan_query(const int64_t* I, int N, int R, const cpg_opts* opts
   return 1;
 }
 
+cpg_status cpg_gradient_plan_set(const int64_t* I, int N, int R, const cpg_opts* opts, const cpg_gradient_plan* plan) {
+  Shape s;
+  if (opts == nullptr || plan == nullptr) return CPG_ERR_ARG;
+  cpg_status st = check_shape(I, N, R, s);
+  if (st != CPG_OK) return st;
+  if (!prec_valid(opts->precision)) return CPG_ERR_ARG;
+  if (plan->split < 1 || plan->split > N - 1 || (opts->split != 0 && opts->split != plan->split)) return CPG_ERR_ARG;
+  GradChoice c;
+  c.k = plan->split;
+  c.fused = plan->fused != 0;
+  if (c.fused && is_tc_prec(opts->precision) && !tc_fused_ok(tc_rank_tile(std::min(R, 64)), tc_code(opts->precision)))
+    return CPG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  g_tuned[tune_key(s, R, opts)] = c;
+  return CPG_OK;
+}
+
+cpg_status cpg_als_plan_set(const int64_t* I, int N, int R, const cpg_opts* opts, const cpg_als_plan* plan) {
+  Shape s;
+  if (opts == nullptr || plan == nullptr) return CPG_ERR_ARG;
+  cpg_status st = check_shape(I, N, R, s);
+  if (st != CPG_OK) return st;
+  if (!prec_valid(opts->precision)) return CPG_ERR_ARG;
+  if (plan->split < 1 || plan->split > N - 1 || (opts->split != 0 && opts->split != plan->split)) return CPG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_tuned_mu);
+  g_als_tuned[tune_key(s, R, opts)] = plan->split;
+  return CPG_OK;
+}
+
 void cpg_autotune_clear(void) {
   std::lock_guard<std::mutex> lock(g_tuned_mu);
   g_tuned.clear();

@@ -67,7 +67,7 @@ struct SimtCfg {
   static constexpr int VECR = RPL < VEC ? RPL : VEC;     // R side: elements per load
   static constexpr int NLD = RPL / VECR;                 // R side: loads per column
   static constexpr int CPW = TK / 8;                     // R side: columns per warp per stage
-  static constexpr int TCL = (TK >= 64 && RT <= 16) ? 2 : 1;  // L side: columns per lane
+  static constexpr int TCL = (TK >= 64 && RT <= 32) ? 2 : 1;  // L side: columns per lane
   static constexpr int WC = TK / (32 * TCL);             // L side: column groups
   static constexpr int WR = 8 / WC;                      // L side: row bands
   static constexpr int ROWS_PW = TJ / WR;                // L side: rows per warp

@@ -293,3 +293,25 @@ def test_noalloc_bound_leaves_out_the_pitched_copy(L):
     st = L.cp_gradient_all_noalloc(dummy, I64, 6, P, 6, P, 0, 0, None)
     assert st != cpgrad.CPG_ERR_WORKSPACE
     assert st == cpgrad.CPG_ERR_CUDA
+
+
+def test_plan_set_arguments(L):
+    """Recorded plans: a valid one is read back, an invalid split or an
+    unsupported fused plan is refused, and clearing forgets both kinds."""
+    cpgrad.autotune_clear()
+    cpgrad.set_gradient_plan([100] * 4, 10, 3, True)
+    assert cpgrad.gradient_plan([100] * 4, 10) == {"split": 3, "fused": True}
+    cpgrad.set_als_plan([100] * 4, 10, 1)
+    assert cpgrad.als_plan([100] * 4, 10) == 1
+    for bad in (0, 4):
+        with pytest.raises(cpgrad.CpgError):
+            cpgrad.set_gradient_plan([100] * 4, 10, bad, False)
+        with pytest.raises(cpgrad.CpgError):
+            cpgrad.set_als_plan([100] * 4, 10, bad)
+    with pytest.raises(cpgrad.CpgError) as e:
+        cpgrad.set_gradient_plan([100] * 4, 10, 2, True, precision="bf16x6")
+    assert e.value.status == cpgrad.CPG_ERR_UNSUPPORTED
+    # the workspace of a gradient covers the recorded plan
+    assert cpgrad.cpg_workspace_size([100] * 4, 10, "fp32", 0, cpgrad.CALL_GRADIENT_ALL) > 0
+    cpgrad.autotune_clear()
+    assert cpgrad.gradient_plan([100] * 4, 10) is None and cpgrad.als_plan([100] * 4, 10) is None
