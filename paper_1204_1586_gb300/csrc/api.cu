@@ -323,9 +323,11 @@ LeadPlan plan_lead(const Shape& s, int R, int k, int sides, int prec) {
   p.RTmax = is_f64(prec) ? kMaxRankTileF64 : kMaxRankTileF32;
   // FP32 step 4 copies Khatri-Rao rows built once per pass only up to rank 32
   // (above, a stage's rows outweigh half its tile and every CTA generates its
-  // own: 0.33 TB/s at R = 64 on 60^5, against 2.7 TB/s at R = 32).  Wider
-  // ranks run as balanced groups of at most 32, one pass over Y each.
-  if (!is_f64(prec) && sides == 1 && R > 32) {
+  // own: 0.33 TB/s at R = 64 on 60^5, against 2.7 TB/s at R = 32), and step 7
+  // keeps two columns per lane only up to rank 32 (0.96 TB/s at R = 64,
+  // 2.6 TB/s at R = 32).  Wider ranks run as balanced groups of at most 32,
+  // one pass over Y each.
+  if (!is_f64(prec) && (sides == 1 || sides == 2) && R > 32) {
     const int ng = (R + 31) / 32;
     p.RTmax = (R + ng - 1) / ng;
   }
