@@ -69,7 +69,7 @@ SimtShape shape(int sides) {
 }  // namespace
 
 #define CPG_F32_INSTANCES(X) \
-  X(4, 256, 128) X(8, 256, 128) X(10, 128, 64) X(12, 128, 64) X(16, 128, 64) X(24, 64, 64) X(32, 64, 64) \
+  X(4, 256, 128) X(8, 256, 128) X(10, 128, 64) X(12, 128, 64) X(16, 128, 64) X(24, 128, 64) X(32, 64, 64) \
   X(48, 32, 32) X(64, 32, 32)
 
 SimtShape simt_shape_f32(int r, int sides) {
