@@ -207,9 +207,11 @@ int cpg_als_candidates(const int64_t* I, int N, int R, const cpg_opts* opts, int
  * written to *chosen (may be NULL).  Later cp_als_iter and cp_ntf_iter calls
  * with opts->split == 0 and the same key run the recorded split whenever
  * their workspace holds it (cpg_workspace_size accounts for it; so do the
- * members of cp_als_batched), else n*.  Workspace:
- * cpg_workspace_size(..., CPG_CALL_ALS_TUNE) bytes, else CPG_ERR_WORKSPACE;
- * argument and precision errors as for cp_als_iter. */
+ * members of cp_als_batched), else n*.  A candidate whose plan cannot run
+ * at this size (refused before any launch) is skipped; CPG_ERR_UNSUPPORTED
+ * when none can.  Workspace: cpg_workspace_size(..., CPG_CALL_ALS_TUNE)
+ * bytes, else CPG_ERR_WORKSPACE; argument and precision errors as for
+ * cp_als_iter. */
 cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const* A, double* lambda, int R,
                             const cpg_opts* opts, int reps, cpg_als_plan* chosen);
 

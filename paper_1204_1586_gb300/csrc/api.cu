@@ -1729,6 +1729,10 @@ cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const*
     if (st != CPG_OK) break;
     o.split = k;
     st = run(1);  // untimed: planning, attribute setup and warm caches
+    if (st == CPG_ERR_UNSUPPORTED) {  // a split this size cannot run (refused before any launch)
+      st = CPG_OK;
+      continue;
+    }
     copy_all(false);
     if (st == CPG_OK && cudaEventRecord(e0, str) != cudaSuccess) st = CPG_ERR_CUDA;
     if (st == CPG_OK) st = run(reps);
@@ -1748,6 +1752,7 @@ cpg_status cpg_autotune_als(const void* Y, const int64_t* I, int N, void* const*
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != CPG_OK) return st;
+  if (best == 0) return CPG_ERR_UNSUPPORTED;  // no candidate could run
   {
     std::lock_guard<std::mutex> lock(g_tuned_mu);
     g_als_tuned[tune_key(s, R, opts)] = best;
