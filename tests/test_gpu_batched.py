@@ -137,3 +137,33 @@ def test_batched_graph_replay(cg, prec):
             assert torch.equal(lams[b], ref[b][0]), b
             assert torch.equal(fits[b], ref[b][1]), b
     assert cg.cpg_device_status(ws) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_batched_runs_recorded_splits(cg, prec):
+    """Members whose CP_ALS split was recorded (as cpg_autotune_als records
+    it) run that split inside cp_als_batched: the same bits as cp_als_iter
+    at that split, and the oracle's normal equations in that split's mode
+    order (backward error, tests/als_checks.py)."""
+    probs = [p for p in mixed_batch(12, seed=77, dtype=np.float32, orders=(3, 4, 5))][:6]
+    splits = [len(p.I) - 1 if oracle.split_point(p.I) != len(p.I) - 1 else 1 for p in probs]
+    cg.autotune_clear()
+    for p, k in zip(probs, splits):
+        cg.set_als_plan(p.I, p.R, k, precision=prec)
+    try:
+        Ys = [torch.from_numpy(p.y).cuda() for p in probs]
+        A_b = [[dev_factor(a, np.float32) for a in p.init] for p in probs]
+        A_s = [[a.clone() for a in A] for A in A_b]
+        cg.cp_als_batched([(Y, p.I, A) for Y, p, A in zip(Ys, probs, A_b)], 1, precision=prec)
+        for Y, p, A, k in zip(Ys, probs, A_s, splits):
+            cg.cp_als_iter(Y, p.I, A, 1, precision=prec, split=k)
+        torch.cuda.synchronize()
+        assert cg.cpg_device_status() == 0
+        for b, (p, k) in enumerate(zip(probs, splits)):
+            assert all(torch.equal(a1, a2) for a1, a2 in zip(A_b[b], A_s[b])), b
+            got = [a.double().cpu().numpy() for a in A_b[b]]
+            errs = sweep_backward_errors(p.y, p.I, [a.astype(np.float32) for a in p.init], got,
+                                         order=oracle.als_mode_order(p.I, k))
+            assert max(errs.values()) <= 1e-5, (b, k, errs)
+    finally:
+        cg.autotune_clear()
